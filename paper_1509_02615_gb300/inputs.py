@@ -1,0 +1,352 @@
+"""Seeded synthetic inputs shared by the CUDA path and the oracle.
+
+This module builds node sets (Cartesian, hexagonal and Poisson-disk scattered
+layouts with their ghost or mirror layers, Sec. 5.1-5.2), the closed-form
+initial states of the test cases (Sec. 6) and the analytic velocity field of
+the scalar-advection case.  It holds none of the RBF-FD arithmetic: no stencil
+selection, no weights, no right-hand side.  Both the CUDA path and the oracle
+import it; neither imports the other.
+
+Node ordering convention (every node set):
+  * prognostic nodes ``[0, n_prog)`` come first (interior and boundary nodes,
+    Sec. 5.2: the PDE is enforced on the boundary, so boundary nodes are
+    stepped), then ghost or mirror nodes ``[n_prog, n_all)``;
+  * ``kind[i]`` for prognostic node i: 0 interior, 1 bottom wall, 2 top wall,
+    3 left wall, 4 right wall;
+  * ``ghost_owner[g]`` is the prognostic boundary node served by ghost
+    ``n_prog + g`` (one ghost per boundary node, Sec. 5.2);
+  * ``src[j]`` maps every node to the prognostic node whose value it carries:
+    the identity on prognostic nodes, the reflected source on mirror nodes
+    (reflection boundary of the advection case, Sec. 6.1); -1 on ghosts, whose
+    values are solved for.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+KIND_INTERIOR, KIND_BOTTOM, KIND_TOP, KIND_LEFT, KIND_RIGHT = 0, 1, 2, 3, 4
+
+# Physical constants of the Navier-Stokes test cases (Sec. 6.2).
+CP, CV, RD, G = 1004.0, 717.0, 287.0, 9.81
+THETA_BAR = 300.0
+
+
+@dataclasses.dataclass
+class NodeSet:
+    x: np.ndarray            # float64 [n_all]
+    z: np.ndarray            # float64 [n_all]  (y for the unit-square case)
+    n_prog: int
+    kind: np.ndarray         # int32 [n_prog]
+    ghost_owner: np.ndarray  # int32 [n_all - n_prog]; -1 for mirror nodes
+    src: np.ndarray          # int32 [n_all]
+    period_x: float          # > 0: periodic in x with this period
+    h: float                 # nominal node spacing
+    layout: str
+    domain: tuple            # (x0, x1, z0, z1)
+
+    @property
+    def n_all(self) -> int:
+        return int(self.x.shape[0])
+
+    @property
+    def n_ghost(self) -> int:
+        return self.n_all - self.n_prog
+
+
+def _lattice_rows(layout, x0, x1, z0, z1, h, periodic_x):
+    """Row positions and per-row x coordinates of a lattice covering the box.
+
+    Hexagonal rows are fitted to the domain height: R = round(H / (h*sqrt(3)/2))
+    intervals of dz = H / R, odd rows shifted by half a column (Sec. 5.1).
+    """
+    W, H = x1 - x0, z1 - z0
+    if layout == "hex":
+        nint = max(1, int(round(H / (h * math.sqrt(3.0) / 2.0))))
+    elif layout == "cart":
+        nint = max(1, int(round(H / h)))
+    else:
+        raise ValueError(layout)
+    dz = H / nint
+    if periodic_x:
+        ncol = int(round(W / h))
+        dx = W / ncol
+    else:
+        ncol = int(round(W / h)) + 1
+        dx = W / (ncol - 1)
+    return nint, dz, ncol, dx
+
+
+def _row_x(layout, r, x0, ncol, dx, periodic_x):
+    c = np.arange(ncol, dtype=np.float64)
+    if layout == "hex" and (r % 2) == 1:
+        if periodic_x:
+            return x0 + (c + 0.5) * dx
+        # walls: odd rows keep the wall nodes and sit half a column inside
+        inner = x0 + (np.arange(ncol - 1) + 0.5) * dx
+        return np.concatenate([[x0], inner, [x0 + (ncol - 1) * dx]])
+    return x0 + c * dx
+
+
+def lattice_nodes(layout: str, x0: float, x1: float, z0: float, z1: float, h: float,
+                  periodic_x: bool = True) -> NodeSet:
+    """Cartesian or hexagonal lattice with one ghost row below and above.
+
+    Each top and bottom wall node gets one ghost one row spacing outside it,
+    straight along the wall normal (Sec. 5.2).  With ``periodic_x`` false the left and right columns are
+    walls as well and get one ghost column outside, continuing the row.  Corner
+    nodes belong to the top or bottom wall.
+    """
+    nint, dz, ncol, dx = _lattice_rows(layout, x0, x1, z0, z1, h, periodic_x)
+    xs, zs, kinds = [], [], []
+    gx, gz, gown = [], [], []
+    for r in range(nint + 1):
+        xr = _row_x(layout, r, x0, ncol, dx, periodic_x)
+        k = np.zeros(xr.shape[0], np.int32)
+        if not periodic_x:
+            k[0], k[-1] = KIND_LEFT, KIND_RIGHT
+        if r == 0:
+            k[:] = KIND_BOTTOM
+        elif r == nint:
+            k[:] = KIND_TOP
+        xs.append(xr)
+        zs.append(np.full(xr.shape[0], z0 + r * dz))
+        kinds.append(k)
+    x = np.concatenate(xs)
+    z = np.concatenate(zs)
+    kind = np.concatenate(kinds)
+    n_prog = x.shape[0]
+    # ghosts: one per wall node, one row spacing outside along the outward
+    # normal.  (Continuing the hexagonal offset instead would make the
+    # periodic ghost system circulant with a zero at the checkerboard mode.)
+    row_start = np.cumsum([0] + [a.shape[0] for a in xs])
+    for r_own, zg in ((0, z0 - dz), (nint, z1 + dz)):
+        own_idx = np.arange(row_start[r_own], row_start[r_own + 1])
+        gx.append(x[own_idx].copy())
+        gz.append(np.full(own_idx.shape[0], zg))
+        gown.append(own_idx)
+    if not periodic_x:
+        for side, kk in ((0, KIND_LEFT), (1, KIND_RIGHT)):
+            own_idx = np.nonzero(kind == kk)[0]
+            xg = x[own_idx] + (-dx if side == 0 else dx)
+            gx.append(xg)
+            gz.append(z[own_idx].copy())
+            gown.append(own_idx)
+    x = np.concatenate([x] + gx)
+    z = np.concatenate([z] + gz)
+    ghost_owner = np.concatenate(gown).astype(np.int32)
+    src = np.concatenate([np.arange(n_prog), -np.ones(x.shape[0] - n_prog, np.int64)]).astype(np.int32)
+    return NodeSet(x=x, z=z, n_prog=n_prog, kind=kind.astype(np.int32), ghost_owner=ghost_owner,
+                   src=src, period_x=(x1 - x0) if periodic_x else 0.0, h=h, layout=layout,
+                   domain=(x0, x1, z0, z1))
+
+
+def density_current_nodes(h: float = 100.0, layout: str = "hex", periodic_x: bool = True) -> NodeSet:
+    """Straka density-current domain [-25.6, 25.6] x [0, 6.4] km (Sec. 6.3)."""
+    return lattice_nodes(layout, -25600.0, 25600.0, 0.0, 6400.0, h, periodic_x)
+
+
+def unit_square_mirrored(m: int = 64, layers: int = 4) -> NodeSet:
+    """Cartesian m x m nodes on [0,1]^2 (boundary nodes included, h = 1/(m-1))
+    plus ``layers`` rows of nodes reflected across each wall and doubly
+    reflected across each corner (Sec. 6.1: reflected nodes carry the values of
+    their interior sources, so no boundary condition is needed)."""
+    h = 1.0 / (m - 1)
+    c = np.arange(m) * h
+    X, Y = np.meshgrid(c, c, indexing="xy")
+    x = X.ravel().copy()
+    y = Y.ravel().copy()
+    n_prog = x.shape[0]
+    gi, gj = np.meshgrid(np.arange(m), np.arange(m), indexing="xy")
+    gi, gj = gi.ravel(), gj.ravel()
+    mx, my, msrc = [], [], []
+
+    def refl(k):
+        # index k in [-layers, m-1+layers] -> source index and coordinate
+        if k < 0:
+            return -k, k * h
+        if k > m - 1:
+            return 2 * (m - 1) - k, k * h
+        return k, k * h
+
+    for jj in range(-layers, m + layers):
+        for ii in range(-layers, m + layers):
+            if 0 <= ii < m and 0 <= jj < m:
+                continue
+            si, xc = refl(ii)
+            sj, yc = refl(jj)
+            mx.append(xc)
+            my.append(yc)
+            msrc.append(sj * m + si)
+    x = np.concatenate([x, np.array(mx)])
+    y = np.concatenate([y, np.array(my)])
+    src = np.concatenate([np.arange(n_prog), np.array(msrc)]).astype(np.int32)
+    kind = np.zeros(n_prog, np.int32)
+    return NodeSet(x=x, z=y, n_prog=n_prog, kind=kind,
+                   ghost_owner=-np.ones(x.shape[0] - n_prog, np.int32), src=src, period_x=0.0,
+                   h=h, layout="cart-mirror", domain=(0.0, 1.0, 0.0, 1.0))
+
+
+def hilbert_order(x: np.ndarray, z: np.ndarray, bits: int = 16) -> np.ndarray:
+    """Permutation sorting points along a Hilbert curve (locality for gathers)."""
+    xs = (x - x.min()) / max(x.max() - x.min(), 1e-300)
+    zs = (z - z.min()) / max(z.max() - z.min(), 1e-300)
+    n = 1 << bits
+    X = np.minimum((xs * (n - 1)).astype(np.int64), n - 1)
+    Y = np.minimum((zs * (n - 1)).astype(np.int64), n - 1)
+    d = np.zeros_like(X)
+    s = n >> 1
+    while s > 0:
+        rx = ((X & s) > 0).astype(np.int64)
+        ry = ((Y & s) > 0).astype(np.int64)
+        d += s * s * ((3 * rx) ^ ry)
+        # rotate
+        flip = ry == 0
+        sw = flip & (rx == 1)
+        X = np.where(sw, s - 1 - X, X)
+        Y = np.where(sw, s - 1 - Y, Y)
+        Xn = np.where(flip, Y, X)
+        Yn = np.where(flip, X, Y)
+        X, Y = Xn, Yn
+        s >>= 1
+    return np.argsort(d, kind="stable")
+
+
+def poisson_disk_nodes(x0: float, x1: float, z0: float, z1: float, h: float, seed: int = 1) -> NodeSet:
+    """Quasi-uniformly scattered nodes (Sec. 5.1) by seeded Bridson sampling.
+
+    Walls carry evenly spaced boundary nodes (spacing h); interior samples keep
+    a minimum distance r_min from each other and at least h/2 from the walls.
+    r_min is chosen so that sqrt(area / N) is close to h.  Each boundary node
+    gets one ghost at distance h outside along the wall normal (corner nodes
+    belong to the bottom/top walls).  Nodes are ordered along a Hilbert curve.
+    """
+    rng = np.random.default_rng(seed)
+    W, H = x1 - x0, z1 - z0
+    nbx = int(round(W / h))
+    nbz = int(round(H / h))
+    bx = x0 + np.arange(nbx + 1) * (W / nbx)
+    bz = z0 + np.arange(1, nbz) * (H / nbz)
+    wall_x = np.concatenate([bx, bx, np.full(bz.shape, x0), np.full(bz.shape, x1)])
+    wall_z = np.concatenate([np.full(bx.shape, z0), np.full(bx.shape, z1), bz, bz])
+    wall_k = np.concatenate([np.full(bx.shape, KIND_BOTTOM), np.full(bx.shape, KIND_TOP),
+                             np.full(bz.shape, KIND_LEFT), np.full(bz.shape, KIND_RIGHT)])
+    # Bridson sampling in the shrunken box with min distance r_min
+    r_min = 0.93 * h
+    cell = r_min / math.sqrt(2.0)
+    gx0, gz0 = x0 + 0.5 * h, z0 + 0.5 * h
+    gW, gH = W - h, H - h
+    ncx, ncz = int(math.ceil(gW / cell)) + 1, int(math.ceil(gH / cell)) + 1
+    grid = -np.ones((ncz, ncx), np.int64)
+    pts = []
+    active = []
+
+    def fits(px, pz):
+        ci, cj = int((px - gx0) / cell), int((pz - gz0) / cell)
+        for jj in range(max(cj - 2, 0), min(cj + 3, ncz)):
+            for ii in range(max(ci - 2, 0), min(ci + 3, ncx)):
+                q = grid[jj, ii]
+                if q >= 0:
+                    qx, qz = pts[q]
+                    if (qx - px) ** 2 + (qz - pz) ** 2 < r_min * r_min:
+                        return False
+        return True
+
+    p0 = (gx0 + rng.uniform() * gW, gz0 + rng.uniform() * gH)
+    pts.append(p0)
+    grid[int((p0[1] - gz0) / cell), int((p0[0] - gx0) / cell)] = 0
+    active.append(0)
+    k_try = 30
+    while active:
+        a = active[rng.integers(len(active))]
+        ax, az = pts[a]
+        placed = False
+        rr = r_min * np.sqrt(rng.uniform(1.0, 4.0, k_try))
+        th = rng.uniform(0.0, 2.0 * math.pi, k_try)
+        for t in range(k_try):
+            px, pz = ax + rr[t] * math.cos(th[t]), az + rr[t] * math.sin(th[t])
+            if not (gx0 <= px <= gx0 + gW and gz0 <= pz <= gz0 + gH):
+                continue
+            if fits(px, pz):
+                pts.append((px, pz))
+                grid[int((pz - gz0) / cell), int((px - gx0) / cell)] = len(pts) - 1
+                active.append(len(pts) - 1)
+                placed = True
+                break
+        if not placed:
+            active.remove(a)
+    ip = np.array(pts)
+    x = np.concatenate([ip[:, 0], wall_x])
+    z = np.concatenate([ip[:, 1], wall_z])
+    kind = np.concatenate([np.zeros(ip.shape[0], np.int32), wall_k.astype(np.int32)])
+    perm = hilbert_order(x, z)
+    x, z, kind = x[perm], z[perm], kind[perm]
+    n_prog = x.shape[0]
+    bidx = np.nonzero(kind != KIND_INTERIOR)[0]
+    nx = np.select([kind[bidx] == KIND_LEFT, kind[bidx] == KIND_RIGHT], [-1.0, 1.0], 0.0)
+    nz = np.select([kind[bidx] == KIND_BOTTOM, kind[bidx] == KIND_TOP], [-1.0, 1.0], 0.0)
+    gx = x[bidx] + h * nx
+    gz = z[bidx] + h * nz
+    return NodeSet(x=np.concatenate([x, gx]), z=np.concatenate([z, gz]), n_prog=n_prog, kind=kind,
+                   ghost_owner=bidx.astype(np.int32),
+                   src=np.concatenate([np.arange(n_prog), -np.ones(bidx.shape[0], np.int64)]).astype(np.int32),
+                   period_x=0.0, h=h, layout="scattered", domain=(x0, x1, z0, z1))
+
+
+# ----------------------------------------------------------------------------
+# Initial states (closed forms of Sec. 6).  Fields are stacked [u, w, theta', pi'].
+# ----------------------------------------------------------------------------
+
+def pibar(z):
+    """Hydrostatic background Exner pressure, 1 - g z / (c_p T_s) (Sec. 6.3)."""
+    return 1.0 - G * np.asarray(z) / (CP * THETA_BAR)
+
+
+def density_current_state(nodes: NodeSet, amp: float = -15.0, xc: float = 0.0, zc: float = 3000.0,
+                          xr: float = 4000.0, zr: float = 2000.0) -> np.ndarray:
+    """Straka cold bubble: T' = amp/2 (1 + cos(pi r)) for r <= 1, theta' = T'/pibar
+    (Sec. 6.3); u = w = pi' = 0.  Returns float64 [4, n_all] (ghosts 0)."""
+    x, z = nodes.x, nodes.z
+    r = np.sqrt(((x - xc) / xr) ** 2 + ((z - zc) / zr) ** 2)
+    tp = np.where(r <= 1.0, 0.5 * amp * (1.0 + np.cos(np.pi * r)), 0.0)
+    U = np.zeros((4, nodes.n_all))
+    U[2] = tp / pibar(z)
+    U[:, nodes.n_prog:] = 0.0
+    return U
+
+
+def warm_bubble_state(nodes: NodeSet, amp: float = 2.0, xc: float = 10000.0, zc: float = 2000.0,
+                      R: float = 2000.0) -> np.ndarray:
+    """Warm bubble theta' = amp cos^2(pi r / (2R)) for r <= R; u = w = pi' = 0."""
+    r = np.hypot(nodes.x - xc, nodes.z - zc)
+    U = np.zeros((4, nodes.n_all))
+    U[2] = np.where(r <= R, amp * np.cos(np.pi * r / (2.0 * R)) ** 2, 0.0)
+    U[:, nodes.n_prog:] = 0.0
+    return U
+
+
+def cosine_bell(x, y, xc=0.25, yc=0.25, radius=0.15):
+    """Cosine bell (1 + cos(pi rt))/2 for rt = dist / radius <= 1 (Sec. 6.1)."""
+    rt = np.hypot(np.asarray(x) - xc, np.asarray(y) - yc) / radius
+    return np.where(rt <= 1.0, 0.5 * (1.0 + np.cos(np.pi * rt)), 0.0)
+
+
+def deformational_velocity(x, y):
+    """Spatial factors of the deformational shear flow
+    u = sin^2(pi x) sin(2 pi y) c(t), v = -sin^2(pi y) sin(2 pi x) c(t),
+    c(t) = cos(pi t / T)."""
+    x = np.asarray(x)
+    y = np.asarray(y)
+    return (np.sin(np.pi * x) ** 2 * np.sin(2 * np.pi * y),
+            -np.sin(np.pi * y) ** 2 * np.sin(2 * np.pi * x))
+
+
+def perturbed_density_current(nodes: NodeSet, seed: int) -> np.ndarray:
+    """Density current with seeded +/-10% amplitude and centre perturbations."""
+    rng = np.random.default_rng(seed)
+    a = -15.0 * (1.0 + rng.uniform(-0.1, 0.1))
+    xc = 0.0 + 4000.0 * rng.uniform(-0.1, 0.1)
+    zc = 3000.0 * (1.0 + rng.uniform(-0.1, 0.1))
+    return density_current_state(nodes, amp=a, xc=xc, zc=zc)
