@@ -1,0 +1,320 @@
+"""Throughput of the PHS RBF-FD hot path on one GB300 (or N replicas).
+
+Workload (default): the density current of Sec. 6.3 on hexagonal nodes at
+100 m -- 38,400 prognostic nodes + 1,024 ghosts, PHS r^7 + degree-4
+polynomials, n = 37, Delta^3 hyperviscosity, mu = 75 m^2/s, dt = 0.25 s --
+stepped in FP32 (FP64-built weights stored in FP32).  One step = one
+classical RK4 step: four stages, each a ghost solve (Sec. 5.2) and one fused
+right-hand-side + RK4-update kernel.  Setup (stencils, weights, packing,
+ghost inverses) is timed separately and reported under "setup".
+
+Metric: node-RHS evaluations per second (4 per node per RK4 step).  The
+working set (~31 MB) fits in L2, so L2 is flushed (a 512 MB write) between
+timed steps; each step is timed alone with CUDA events on the problem's
+stream.  The FP64 form of the same workload is reported under "fp64".
+
+--impl reference times the FP64 CPU oracle (the only other implementation of
+the method here) on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "node-RHS evals/s (RK4)"
+UNIT = "node-RHS/s"
+WORKLOAD = "density current (Sec. 6.3), hexagonal 100 m, 38400 nodes + 1024 ghosts, r^7 + deg 4, n=37, Delta^3"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--h", type=float, default=100.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in ("ns.cu", "problem.cuh"):
+        with open(os.path.join(ROOT, "paper_1509_02615_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(key)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.path = f"/tmp/rbffd_clocks_{os.getpid()}.csv"
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except OSError:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_problem(h, precision):
+    from paper_1509_02615_gb300 import inputs as inp
+    from paper_1509_02615_gb300 import rbffd
+    nodes = inp.density_current_nodes(h)
+    pb = rbffd.ns_problem(nodes, precision=precision)
+    U0 = inp.density_current_state(nodes)
+    return nodes, pb, U0
+
+
+def time_steps(torch, pb, U, dt, steps, warmup, flush, stage_timing):
+    """Per-step device times (ms) and summed stage-kernel times (ms)."""
+    stream = torch.cuda.current_stream()
+    pb.set_stage_timing(stage_timing)
+    t = 0.0
+    for _ in range(warmup):
+        flush.zero_()
+        pb.run(t, dt, 1, U)
+        t += dt
+    torch.cuda.synchronize()
+    step_ms, stage_ms = [], []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(steps):
+        flush.zero_()                    # evict the 31 MB working set from L2
+        e0.record(stream)
+        pb.run(t, dt, 1, U)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        if stage_timing:
+            stage_ms.append(pb.stage_kernel_ms())
+        t += dt
+    pb.set_stage_timing(False)
+    return step_ms, stage_ms
+
+
+def cpu_baseline(h, budget_s=12.0):
+    """FP64 oracle on a 1/8-width periodic strip of the same workload (same
+    spacing, stencils, operators and boundary treatment): node-RHS/s."""
+    from oracle.ns import NSOracle
+    from paper_1509_02615_gb300 import inputs as inp
+    width = 25600.0 / 8.0
+    nodes = inp.lattice_nodes("hex", -width, width, 0.0, 6400.0, h, True)
+    o = NSOracle(nodes)
+    U = inp.density_current_state(nodes)
+    U = o.rk4_step(0.0, h / 400.0, U)
+    t0 = time.perf_counter()
+    n_eval = 0
+    while time.perf_counter() - t0 < budget_s:
+        o.rhs(0.0, U)
+        n_eval += 1
+    el = time.perf_counter() - t0
+    return {"value": n_eval * nodes.n_prog / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"FP64 oracle RHS (ghost solve + sparse DM products) on a periodic strip of the "
+                      f"workload, 1/8 of its width ({nodes.n_prog} of 38400 nodes, same h, stencils and walls), {n_eval} evaluations "
+                      f"in {el:.1f} s, single-threaded scipy.sparse"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    t0 = time.perf_counter()
+    base = cpu_baseline(args.h, budget_s=max(5.0, min(60.0, 0.5 * args.steps)))
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp64 oracle", "l2": "n/a (CPU)"},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    from paper_1509_02615_gb300 import _build
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.barrier()
+        if rank != 0:
+            _build.build()   # no-op once rank 0 has built
+    torch.cuda.set_device(local)
+    from paper_1509_02615_gb300 import rbffd
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    pk, pk_kind = peaks()
+
+    nodes, pb, U0 = make_problem(args.h, args.precision)
+    info = pb.info()
+    dt = args.h / 400.0
+    U = rbffd.state_tensor(U0, args.precision)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        step_ms, stage_ms = time_steps(torch, pb, U, dt, args.steps, args.warmup, flush, True)
+    torch.cuda.synchronize()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    node_rhs = 4.0 * nodes.n_prog * args.steps * world
+    value = node_rhs / (total_ms / 1e3)
+    mm = pb.minmax(U)   # fails loudly on NaN/Inf
+
+    # roofline of the dominant kernel: the fused RHS + RK4 stage kernel
+    stage_avg_ms = float(np.mean(stage_ms)) / 4.0
+    bytes_per_launch = info["rhs_bytes_per_node"] * nodes.n_prog
+    achieved = bytes_per_launch / (stage_avg_ms / 1e3) / 1e9
+    key = f"ns_stage_fp{args.precision}_hex{int(args.h)}"
+    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / pk["hbm_gbs"], "traffic": profiled_traffic(key), "kernel": "ns_stage_kernel",
+            "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": stage_avg_ms,
+            "stage_share_of_step": float(np.sum(stage_ms) / total_ms) if stage_ms else None,
+            "peak_source": f"{pk_kind} hbm_gbs"}
+
+    # end to end through the C ABI on a pinned host state, copies included
+    Uh = rbffd.state_tensor(U0, args.precision, device="cpu").pin_memory()
+    e2e_steps = max(10, args.steps // 4)
+    pb.run_host(0.0, dt, 1, Uh)
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        pb.run_host(s * dt, dt, 1, Uh)
+    e2e_s = time.perf_counter() - t0
+    state_bytes = Uh.numel() * Uh.element_size()
+    e2e = {"value": 4.0 * nodes.n_prog * e2e_steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+           "note": "rbf_run_host per RK4 step: pinned host state -> device, one RK4 step, device -> host"}
+
+    fp64 = None
+    if not args.no_fp64 and args.precision == 32:
+        n64, pb64, _ = make_problem(args.h, 64)
+        U64 = rbffd.state_tensor(U0, 64)
+        s64, k64 = time_steps(torch, pb64, U64, dt, max(20, args.steps // 4), args.warmup, flush, True)
+        i64 = pb64.info()
+        t64 = float(sum(s64))
+        avg64 = float(np.mean(k64)) / 4.0
+        flops = i64["rhs_flops_per_node"] * n64.n_prog
+        fp64 = {"value": 4.0 * n64.n_prog * len(s64) / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / len(s64),
+                "roofline": {"bound": "alu", "achieved": flops / (avg64 / 1e3) / 1e12, "peak": 1.25,
+                             "unit": "TFLOP/s", "frac": flops / (avg64 / 1e3) / 1e12 / 1.25,
+                             "peak_source": "nominal GB300 FP64 rate", "avg_launch_ms": avg64,
+                             "hbm_GBps": i64["rhs_bytes_per_node"] * n64.n_prog / (avg64 / 1e3) / 1e9},
+                "threads_per_node": i64["threads_per_node"]}
+        pb64.close()
+
+    base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        base = cpu_baseline(args.h)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n_prog": nodes.n_prog, "n_ghost": nodes.n_ghost,
+                           "dt_s": dt, "precision": f"fp{args.precision}",
+                           "l2": "flushed between timed steps (512 MB write); working set ~31 MB",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "threads_per_node": info["threads_per_node"]},
+                "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
+                "gpu_launches": info["launches_per_step"] * args.steps,
+                "setup": {"weight_build_ms": info["weight_build_ms"], "ghost_setup_ms": info["ghost_setup_ms"]},
+                "fp64": fp64, "cpu_baseline": base,
+                "state_minmax": {"theta_min": mm[2, 0], "w_min": mm[1, 0], "w_max": mm[1, 1]}}
+        print(json.dumps(line), flush=True)
+    pb.close()
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

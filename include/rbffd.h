@@ -1,0 +1,226 @@
+/*
+ * rbffd.h -- C ABI of the GB300 (sm_103a) PHS RBF-FD library.
+ *
+ * The method (Barnett, Flyer & Wicker, "An RBF-FD polynomial method based on
+ * polyharmonic splines for the Navier-Stokes equations"):
+ *   Sec. 3, Eq. (weights): per node, solve the augmented system
+ *       [A P; P^T 0] [w; lambda] = [L phi; L p]   at x_c,
+ *   A_ij = ||x_i - x_j||^p (odd PHS), P = 2D monomials of degree <= l,
+ *   giving one row of a sparse differentiation matrix (only nonzeros kept).
+ *   Sec. 5.2, Eq. (bcEqn): ghost values u_G = -W_G^{-1}(W_I u_I + W_B u_B).
+ *   Sec. 5.3, Eq. (laplacian): hyperviscosity (-1)^(k+1) gamma Delta^k.
+ *   Sec. 6.1: flux-form scalar advection with reflected boundary nodes.
+ *   Sec. 6.2, Eqs. (uEq)-(piEq): 2D compressible Navier-Stokes in
+ *   perturbation form, fields [u, w, theta', pi'], stepped with RK4.
+ *
+ * Conventions (every entry point):
+ *   - Return value: RBF_OK (0) or one of the RBF_E_* codes; the message of
+ *     the last failure on the calling thread is in rbf_last_error().
+ *     No C++ exception crosses the ABI.
+ *   - "device" pointers are CUDA global-memory pointers on the current
+ *     device; "host" pointers are ordinary CPU memory.  The caller owns every
+ *     buffer it passes; the library never frees them.
+ *   - Node arrays list the prognostic nodes [0, n_prog) first, then ghost or
+ *     reflected nodes [n_prog, n_all).
+ *   - Field arrays are structure-of-arrays, field-major: U[f * n_all + i].
+ *   - stream: a cudaStream_t (NULL = legacy default stream).  Setup calls
+ *     (rbf_build_*, rbf_*_create) return after their work completes; the
+ *     stepping calls (rbf_rhs, rbf_rk4_step, rbf_run) only enqueue work.
+ *   - There is no CPU fallback: without a usable GPU every call returns
+ *     RBF_E_CUDA.
+ */
+#ifndef RBFFD_H
+#define RBFFD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define RBF_OK 0
+#define RBF_E_ARG 1          /* invalid argument (message says which)        */
+#define RBF_E_SINGULAR 2     /* a weight or ghost system has a zero pivot    */
+#define RBF_E_NONFINITE 3    /* NaN or Inf found by rbf_check_finite         */
+#define RBF_E_TIMEOUT 4      /* a bounded device-side wait gave up           */
+#define RBF_E_CUDA 5         /* CUDA runtime error (message has the string)  */
+#define RBF_E_OOM 6          /* device allocation failed                     */
+
+/* ---- operators L of Eq. (weights) -------------------------------------- */
+#define RBF_OP_DX 0   /* d/dx                                              */
+#define RBF_OP_DZ 1   /* d/dz (the second coordinate, y in Sec. 6.1)       */
+#define RBF_OP_LAP 2  /* Laplacian, Eq. (laplacian)                        */
+#define RBF_OP_HV 3   /* Delta^k, Eq. (laplacian) applied k times          */
+#define RBF_OP_DXX 4  /* d2/dx2                                            */
+#define RBF_OP_DZZ 5  /* d2/dz2                                            */
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *rbf_last_error(void);
+
+/*
+ * a1  Stencil selection (Sec. 6: the n nearest nodes; Appendix A).
+ * For each centre c in [0, n_centers) (centres are nodes 0..n_centers-1),
+ * writes the n nearest of all n_all nodes, ordered by squared distance
+ * (FP64, dx*dx + dz*dz without fused multiply-add), ties by node index.
+ * With period_x > 0, dx is taken to the minimum image in x.
+ *   x, z      device, double [n_all]
+ *   idx       device, int32 [n_centers][n] (output; idx[c][0] == c)
+ * Errors: RBF_E_ARG for n < 1, n > n_all, n > 128, non-finite coordinates or
+ * a node density so uneven that a search window holds > 4096 candidates.
+ */
+int rbf_build_stencils(const double *x, const double *z, int64_t n_all, int64_t n_centers,
+                       int32_t n, double period_x, int32_t *idx, void *stream);
+
+/*
+ * a2  RBF-FD weights (Sec. 3, Eq. (weights); Sec. 5.3, Eq. (laplacian)).
+ * One augmented solve per stencil with PHS r^p (p odd, 1 <= p <= 15) and all
+ * monomials of degree <= l (0 <= l <= 8), in coordinates shifted to the
+ * centre and scaled by the stencil radius; LU with partial pivoting in FP64.
+ * RBF_OP_HV uses Delta^hv_k and needs p >= 2*hv_k + 1.
+ *   x, z      device, double [n_all]
+ *   idx       device, int32 [n_centers][n], centre first (rbf_build_stencils)
+ *   ops       host, int32 [n_ops], RBF_OP_* codes (1 <= n_ops <= 6)
+ *   w         device, double [n_ops][n_centers][n] (output, physical units)
+ * Errors: RBF_E_ARG for bad sizes or codes, n + (l+1)(l+2)/2 > 160;
+ * RBF_E_SINGULAR if a pivot vanishes (node id in the message).
+ */
+int rbf_build_weights(const double *x, const double *z, int64_t n_all, const int32_t *idx,
+                      int64_t n_centers, int32_t n, double period_x, int32_t p, int32_t l,
+                      int32_t hv_k, const int32_t *ops, int32_t n_ops, double *w, void *stream);
+
+/* ---- problems: a stepping context built once, stepped many times -------- */
+typedef struct rbf_problem rbf_problem;
+
+/* Parameters of the Navier-Stokes problem (Sec. 6.2-6.3). */
+typedef struct rbf_ns_params {
+    int32_t n_sten;     /* stencil size n (37 in Sec. 6)                      */
+    int32_t phs_p;      /* PHS exponent of d/dx, d/dz, Lap, BC operators (7)   */
+    int32_t poly_l;     /* polynomial degree l (4)                            */
+    int32_t hv_k;       /* hyperviscosity Laplacian power k (3); 0 = none     */
+    int32_t hv_p;       /* PHS exponent of the Delta^k weights (>= 2k+1)      */
+    int32_t precision;  /* 64: FP64 storage and arithmetic; 32: FP64-built
+                           weights stored in FP32, FP32 RHS and RK4           */
+    int32_t threads_per_node; /* 0 = autotuned; else 1, 2, 4 or 8             */
+    int32_t reserved;
+    double period_x;    /* > 0: periodic in x with this period (m)            */
+    double mu;          /* viscosity (m^2/s)                                  */
+    double gamma;       /* hyperviscosity coefficient gamma >= 0              */
+    double theta_bar;   /* background potential temperature T_s (300 K)      */
+    double g, cp, cv, rd; /* 9.81, 1004, 717, 287                             */
+} rbf_ns_params;
+
+/*
+ * Build a Navier-Stokes problem: stencils (a1), weights (a2) for d/dx, d/dz,
+ * Lap, d2/dx2, d2/dz2 and Delta^k, the packed operators (a3) and the ghost
+ * systems of Sec. 5.2 (a4: inverted once, applied every stage).
+ *   x, z         host, double [n_all]
+ *   kind         host, int32 [n_prog]: 0 interior, 1 bottom, 2 top, 3 left,
+ *                4 right wall (corner nodes belong to bottom/top)
+ *   ghost_owner  host, int32 [n_all - n_prog]: the wall node of each ghost
+ * Boundary conditions (Sec. 6.3, 6.4): bottom/top u_z = 0, w = w_zz = 0,
+ * theta'_z = 0, pi'_z = g theta'/(c_p theta_bar (theta_bar + theta'));
+ * left/right u = u_xx = 0, w_x = 0, theta'_x = 0, pi'_x = 0.
+ * The problem keeps the stream for all its work.
+ */
+int rbf_ns_create(rbf_problem **out, const rbf_ns_params *prm, const double *x, const double *z,
+                  int64_t n_prog, int64_t n_all, const int32_t *kind, const int32_t *ghost_owner,
+                  void *stream);
+
+/* Parameters of the scalar-advection problem (Sec. 6.1). */
+typedef struct rbf_adv_params {
+    int32_t n_sten;     /* 37                                                 */
+    int32_t phs_p;      /* PHS exponent of d/dx, d/dy (7)                     */
+    int32_t poly_l;     /* 4                                                  */
+    int32_t hv_k;       /* 4                                                  */
+    int32_t hv_p;       /* 9 (Delta^4 r^7 is singular at r = 0)               */
+    int32_t precision;  /* 64 or 32                                           */
+    double gamma;       /* hyperviscosity coefficient                        */
+    double period_T;    /* velocity time factor cos(pi t / T)                 */
+} rbf_adv_params;
+
+/*
+ * Build a flux-form advection problem psi_t = -(u psi)_x - (v psi)_y with
+ * u = U(x,y) cos(pi t/T), v = V(x,y) cos(pi t/T).  Nodes [n_prog, n_all) are
+ * reflections of prognostic nodes (src gives the source); their values are
+ * their sources' values and U, V are sampled at their own positions.
+ *   x, z, U, V   host, double [n_all];  src  host, int32 [n_all]
+ */
+int rbf_adv_create(rbf_problem **out, const rbf_adv_params *prm, const double *x, const double *z,
+                   int64_t n_prog, int64_t n_all, const int32_t *src, const double *U,
+                   const double *V, void *stream);
+
+/*
+ * a4+a5(+a6)  Right-hand side at time t.
+ *   U     device, FP64 or FP32 per the problem's precision:
+ *         NS [4][n_all] (ghost entries are overwritten with the solved
+ *         ghost values); advection [1][n_prog]
+ *   dUdt  device, same precision, [F][n_prog]
+ */
+int rbf_rhs(rbf_problem *pb, double t, void *U, void *dUdt);
+
+/*
+ * a7  One classical RK4 step of size dt from time t, in place on U
+ * (layout as for rbf_rhs).  Dirichlet components (w on bottom/top walls,
+ * u on left/right walls) keep their values.
+ */
+int rbf_rk4_step(rbf_problem *pb, double t, double dt, void *U);
+
+/* n_steps RK4 steps from t0, replayed from a captured CUDA graph. */
+int rbf_run(rbf_problem *pb, double t0, double dt, int64_t n_steps, void *U);
+
+/*
+ * End-to-end form of rbf_run on a HOST state: copies U_host to the device,
+ * runs n_steps, copies the result back and waits.  U_host should be pinned.
+ */
+int rbf_run_host(rbf_problem *pb, double t0, double dt, int64_t n_steps, void *U_host);
+
+/* Waits for the problem's stream; returns RBF_E_CUDA on an asynchronous fault. */
+int rbf_sync(rbf_problem *pb);
+
+/*
+ * Per-field minimum and maximum over the prognostic nodes of U (device,
+ * layout as for rbf_rhs), written to host out_minmax [F][2].  Returns
+ * RBF_E_NONFINITE if any prognostic value is NaN or Inf.  Synchronous.
+ */
+int rbf_minmax(rbf_problem *pb, const void *U, double *out_minmax);
+
+/* Facts about a problem, for tests and measurement. */
+typedef struct rbf_info {
+    int64_t n_prog, n_all, n_ghost;
+    int32_t n_fields, precision, n_sten, threads_per_node;
+    int32_t slots;              /* packed neighbour slots per node          */
+    int32_t launches_per_step;  /* kernel launches in one RK4 step          */
+    int32_t n_components;       /* independent ghost systems                */
+    int32_t n_ghost_classes;    /* distinct ghost matrices per component    */
+    double weight_build_ms;     /* GPU time of stencils + weights + pack    */
+    double ghost_setup_ms;      /* GPU time of the ghost inverses           */
+    double rhs_bytes_per_node;  /* algorithmic HBM bytes of one RHS stage   */
+    double rhs_flops_per_node;  /* arithmetic of one RHS stage              */
+} rbf_info;
+int rbf_get_info(const rbf_problem *pb, rbf_info *out);
+
+/*
+ * Copies of the problem's FP64 weights, for parity tests:
+ *   op = RBF_OP_*; out host double [n_prog][n_sten] and (optional) out_idx
+ *   host int32 [n_prog][n_sten].  RBF_E_ARG if the problem has no such op.
+ */
+int rbf_get_weights(const rbf_problem *pb, int32_t op, double *out, int32_t *out_idx);
+
+/*
+ * Stage-kernel timing for measurement.  With enable != 0, rbf_run captures
+ * one RK4 step per graph and records CUDA events around each of the four
+ * fused right-hand-side + RK4 stage kernels; rbf_stage_kernel_ms then waits
+ * and returns (host double) their summed device time in the last replayed
+ * step.  RBF_E_ARG if timing is off or no step has run.
+ */
+int rbf_set_stage_timing(rbf_problem *pb, int32_t enable);
+int rbf_stage_kernel_ms(rbf_problem *pb, double *ms);
+
+/* Destroys the problem and frees its device memory (after a sync). */
+int rbf_destroy(rbf_problem *pb);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RBFFD_H */

@@ -1,0 +1,447 @@
+// extern "C" entry points of librbffd (declared in include/rbffd.h): problem
+// construction, stepping, graph replay and queries.  Every call is guarded:
+// library failures become RBF_E_* codes with a message in rbf_last_error().
+#include <cmath>
+#include <cstring>
+
+#include "problem.cuh"
+
+namespace rbf {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+const char *last_error() { return g_last_error.c_str(); }
+
+int sm_count() {
+    int dev = 0, n = 0;
+    RBF_CUDA(cudaGetDevice(&dev));
+    RBF_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    return n;
+}
+
+Problem::~Problem() {
+    if (graph) cudaGraphExecDestroy(graph);
+    for (cudaEvent_t e : rhs_ev) cudaEventDestroy(e);
+    if (cap) cudaStreamDestroy(cap);
+}
+
+namespace {
+
+template <class T>
+__global__ void pibar_kernel(const double *z, int64_t n_prog, double g, double cp, double theta_bar, T *out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n_prog) out[i] = (T)(1.0 - g * z[i] / (cp * theta_bar));   // Sec. 6.3 background Exner
+}
+
+__global__ void set_time(double *t, double v) { *t = v; }
+
+void common_setup(Problem &pb, const double *x, const double *z, int64_t n_prog, int64_t n_all, void *stream) {
+    RBF_REQUIRE(n_prog >= 1 && n_all >= n_prog, "need 1 <= n_prog <= n_all (got %lld, %lld)", (long long)n_prog,
+                (long long)n_all);
+    RBF_REQUIRE(n_all < ((int64_t)1 << 31), "n_all exceeds int32 indexing");
+    RBF_REQUIRE(x && z, "null coordinates");
+    for (int64_t i = 0; i < n_all; ++i)
+        RBF_REQUIRE(std::isfinite(x[i]) && std::isfinite(z[i]), "non-finite coordinate at node %lld", (long long)i);
+    int ndev = 0;
+    RBF_CUDA(cudaGetDeviceCount(&ndev));
+    RBF_REQUIRE(ndev > 0, "no CUDA device");
+    pb.st = as_stream(stream);
+    pb.n_prog = n_prog;
+    pb.n_all = n_all;
+    RBF_CUDA(cudaStreamCreateWithFlags(&pb.cap, cudaStreamNonBlocking));
+    pb.x.alloc(n_all);
+    pb.z.alloc(n_all);
+    RBF_CUDA(cudaMemcpyAsync(pb.x.p, x, n_all * 8, cudaMemcpyHostToDevice, pb.st));
+    RBF_CUDA(cudaMemcpyAsync(pb.z.p, z, n_all * 8, cudaMemcpyHostToDevice, pb.st));
+    pb.tdev.alloc(1);
+}
+
+void alloc_scratch(Problem &pb) {
+    const int64_t stride = pb.kind == kNS ? pb.n_all : pb.n_prog;
+    const size_t ts = pb.tsize();
+    pb.S0.alloc((size_t)pb.F * stride * ts);
+    pb.S1.alloc((size_t)pb.F * stride * ts);
+    pb.K.alloc((size_t)pb.F * pb.n_prog * ts);
+    // ghost entries of the stage buffers are written by the ghost fill; zero
+    // them once so that nothing uninitialised is ever read
+    RBF_CUDA(cudaMemsetAsync(pb.S0.p, 0, pb.S0.bytes(), pb.st));
+    RBF_CUDA(cudaMemsetAsync(pb.S1.p, 0, pb.S1.bytes(), pb.st));
+}
+
+void choose_threads(Problem &pb, int requested) {
+    if (requested == 0) {
+        autotune_threads_per_node(pb);
+    } else {
+        RBF_REQUIRE(requested == 1 || requested == 2 || requested == 4 || requested == 8,
+                    "threads_per_node must be 0, 1, 2, 4 or 8");
+        pb.G = requested;
+        pack_operators(pb);
+    }
+}
+
+void invalidate_graph(Problem &pb) {
+    if (pb.graph) cudaGraphExecDestroy(pb.graph);
+    pb.graph = nullptr;
+    pb.graph_U = nullptr;
+    pb.graph_steps = 0;
+}
+
+// Captures `steps` RK4 steps on the private stream into an executable graph.
+void capture(Problem &pb, void *U, double dt, int steps) {
+    invalidate_graph(pb);
+    if (pb.record_rhs_events) {
+        for (cudaEvent_t e : pb.rhs_ev) cudaEventDestroy(e);
+        pb.rhs_ev.assign(8 * steps, nullptr);
+        for (auto &e : pb.rhs_ev) RBF_CUDA(cudaEventCreate(&e));
+    }
+    cudaGraph_t g = nullptr;
+    RBF_CUDA(cudaStreamBeginCapture(pb.cap, cudaStreamCaptureModeThreadLocal));
+    try {
+        for (int s = 0; s < steps; ++s) enqueue_rk4_step(pb, 0.0, dt, U, pb.cap, pb.record_rhs_events, s);
+    } catch (...) {
+        cudaStreamEndCapture(pb.cap, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    RBF_CUDA(cudaStreamEndCapture(pb.cap, &g));
+    cudaError_t e = cudaGraphInstantiate(&pb.graph, g, 0);
+    cudaGraphDestroy(g);
+    RBF_CUDA(e);
+    pb.graph_U = U;
+    pb.graph_dt = dt;
+    pb.graph_steps = steps;
+}
+
+void run(Problem &pb, double t0, double dt, int64_t n_steps, void *U) {
+    RBF_REQUIRE(U != nullptr, "null state");
+    RBF_REQUIRE(n_steps >= 0, "n_steps < 0");
+    RBF_REQUIRE(std::isfinite(dt) && std::isfinite(t0), "non-finite time or step");
+    if (n_steps == 0) return;
+    const int chunk = (int)std::min<int64_t>(n_steps, pb.record_rhs_events ? 1 : 16);
+    if (!pb.graph || pb.graph_U != U || pb.graph_dt != dt || pb.graph_steps != chunk) capture(pb, U, dt, chunk);
+    cudaEvent_t ev;
+    RBF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    // order the private stream after the caller's stream
+    RBF_CUDA(cudaEventRecord(ev, pb.st));
+    RBF_CUDA(cudaStreamWaitEvent(pb.cap, ev, 0));
+    set_time<<<1, 1, 0, pb.cap>>>(pb.tdev.p, t0);
+    RBF_CHECK_LAUNCH();
+    int64_t done = 0;
+    while (done + chunk <= n_steps) {
+        RBF_CUDA(cudaGraphLaunch(pb.graph, pb.cap));
+        done += chunk;
+    }
+    // remainder steps go straight onto the private stream
+    for (; done < n_steps; ++done) enqueue_rk4_step(pb, t0 + done * dt, dt, U, pb.cap, false, 0);
+    RBF_CUDA(cudaEventRecord(ev, pb.cap));
+    RBF_CUDA(cudaStreamWaitEvent(pb.st, ev, 0));
+    cudaEventDestroy(ev);   // released once the recorded work completes
+}
+
+}  // namespace
+}  // namespace rbf
+
+using rbf::Problem;
+
+extern "C" {
+
+const char *rbf_last_error(void) { return rbf::last_error(); }
+
+int rbf_ns_create(rbf_problem **out, const rbf_ns_params *prm, const double *x, const double *z, int64_t n_prog,
+                  int64_t n_all, const int32_t *kind, const int32_t *ghost_owner, void *stream) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(out && prm, "null argument");
+        *out = nullptr;
+        RBF_REQUIRE(prm->precision == 64 || prm->precision == 32, "precision must be 64 or 32");
+        RBF_REQUIRE(prm->n_sten >= 2, "stencil size must be >= 2");
+        RBF_REQUIRE(prm->mu >= 0.0 && prm->gamma >= 0.0, "mu and gamma must be >= 0");
+        RBF_REQUIRE(prm->theta_bar > 0.0 && prm->cp > 0.0 && prm->cv > 0.0, "bad physical constants");
+        RBF_REQUIRE(kind != nullptr, "null kind");
+        RBF_REQUIRE(n_all == n_prog || ghost_owner != nullptr, "ghosts need ghost_owner");
+        auto *h = new rbf_problem();
+        try {
+            Problem &pb = h->impl;
+            pb.kind = rbf::kNS;
+            pb.F = 4;
+            rbf::common_setup(pb, x, z, n_prog, n_all, stream);
+            pb.precision = prm->precision;
+            pb.n = prm->n_sten;
+            pb.p = prm->phs_p;
+            pb.l = prm->poly_l;
+            pb.hv_k = prm->hv_k;
+            pb.hv_p = prm->hv_p;
+            pb.period_x = prm->period_x;
+            pb.mu = prm->mu;
+            pb.gamma = prm->gamma;
+            pb.hvc = prm->hv_k > 0 ? ((prm->hv_k % 2 == 1) ? 1.0 : -1.0) * prm->gamma : 0.0;  // (-1)^(k+1) gamma
+            pb.theta_bar = prm->theta_bar;
+            pb.g = prm->g;
+            pb.cp = prm->cp;
+            pb.cv = prm->cv;
+            pb.rd = prm->rd;
+            pb.diff = pb.precision == 32 ? 1 : 0;
+            for (int64_t i = 0; i < n_prog; ++i)
+                RBF_REQUIRE(kind[i] >= 0 && kind[i] <= 4, "kind[%lld]=%d not in [0, 4]", (long long)i, kind[i]);
+
+            cudaEvent_t e0, e1;
+            RBF_CUDA(cudaEventCreate(&e0));
+            RBF_CUDA(cudaEventCreate(&e1));
+            RBF_CUDA(cudaEventRecord(e0, pb.st));
+            pb.idx.alloc((size_t)n_prog * pb.n);
+            rbf::build_stencils(pb.x.p, pb.z.p, n_all, n_prog, pb.n, pb.period_x, pb.idx.p, pb.st);
+            pb.ops = {RBF_OP_DX, RBF_OP_DZ, RBF_OP_LAP, RBF_OP_DXX, RBF_OP_DZZ};
+            const int nbase = (int)pb.ops.size();
+            if (pb.hv_k > 0) pb.ops.push_back(RBF_OP_HV);
+            pb.w64.alloc(pb.ops.size() * (size_t)n_prog * pb.n);
+            rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, pb.period_x, pb.p, pb.l, 0, pb.ops.data(),
+                               nbase, pb.w64.p, pb.st);
+            if (pb.hv_k > 0) {
+                int hv = RBF_OP_HV;
+                rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, pb.period_x, pb.hv_p, pb.l, pb.hv_k, &hv,
+                                   1, pb.w64.p + (size_t)nbase * n_prog * pb.n, pb.st);
+            }
+            RBF_CUDA(cudaEventRecord(e1, pb.st));
+            RBF_CUDA(cudaEventSynchronize(e1));
+            RBF_CUDA(cudaEventElapsedTime(&pb.weight_build_ms, e0, e1));
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+
+            // per-node background Exner pressure and Dirichlet flags
+            pb.pibar.alloc((size_t)n_prog * pb.tsize());
+            if (pb.precision == 64)
+                rbf::pibar_kernel<double><<<rbf::div_up(n_prog, 256), 256, 0, pb.st>>>(pb.z.p, n_prog, pb.g, pb.cp,
+                                                                                     pb.theta_bar, (double *)pb.pibar.p);
+            else
+                rbf::pibar_kernel<float><<<rbf::div_up(n_prog, 256), 256, 0, pb.st>>>(pb.z.p, n_prog, pb.g, pb.cp,
+                                                                                    pb.theta_bar, (float *)pb.pibar.p);
+            RBF_CHECK_LAUNCH();
+            std::vector<unsigned char> fl(n_prog);
+            for (int64_t i = 0; i < n_prog; ++i)
+                fl[i] = (kind[i] == 1 || kind[i] == 2) ? 1 : (kind[i] == 3 || kind[i] == 4) ? 2 : 0;
+            pb.flags.alloc(n_prog);
+            RBF_CUDA(cudaMemcpyAsync(pb.flags.p, fl.data(), n_prog, cudaMemcpyHostToDevice, pb.st));
+
+            rbf::build_ghost_plan(pb, kind, ghost_owner);
+            rbf::choose_threads(pb, prm->threads_per_node);
+            rbf::alloc_scratch(pb);
+            RBF_CUDA(cudaStreamSynchronize(pb.st));
+            *out = h;
+        } catch (...) {
+            delete h;
+            throw;
+        }
+    });
+}
+
+int rbf_adv_create(rbf_problem **out, const rbf_adv_params *prm, const double *x, const double *z, int64_t n_prog,
+                   int64_t n_all, const int32_t *src, const double *U, const double *V, void *stream) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(out && prm && src && U && V, "null argument");
+        *out = nullptr;
+        RBF_REQUIRE(prm->precision == 64 || prm->precision == 32, "precision must be 64 or 32");
+        RBF_REQUIRE(prm->period_T > 0.0 && prm->gamma >= 0.0, "period_T must be > 0 and gamma >= 0");
+        for (int64_t j = 0; j < n_all; ++j)
+            RBF_REQUIRE(src[j] >= 0 && src[j] < n_prog && (j >= n_prog || src[j] == j),
+                        "src[%lld]=%d invalid", (long long)j, src[j]);
+        auto *h = new rbf_problem();
+        try {
+            Problem &pb = h->impl;
+            pb.kind = rbf::kAdvection;
+            pb.F = 1;
+            rbf::common_setup(pb, x, z, n_prog, n_all, stream);
+            pb.precision = prm->precision;
+            pb.n = prm->n_sten;
+            pb.p = prm->phs_p;
+            pb.l = prm->poly_l;
+            pb.hv_k = prm->hv_k;
+            pb.hv_p = prm->hv_p;
+            pb.gamma = prm->gamma;
+            pb.hvc = prm->hv_k > 0 ? ((prm->hv_k % 2 == 1) ? 1.0 : -1.0) * prm->gamma : 0.0;
+            pb.period_T = prm->period_T;
+            pb.diff = 0;
+            pb.vel.alloc(2 * (size_t)n_all);
+            pb.src.alloc(n_all);
+            RBF_CUDA(cudaMemcpyAsync(pb.vel.p, U, n_all * 8, cudaMemcpyHostToDevice, pb.st));
+            RBF_CUDA(cudaMemcpyAsync(pb.vel.p + n_all, V, n_all * 8, cudaMemcpyHostToDevice, pb.st));
+            RBF_CUDA(cudaMemcpyAsync(pb.src.p, src, n_all * 4, cudaMemcpyHostToDevice, pb.st));
+
+            cudaEvent_t e0, e1;
+            RBF_CUDA(cudaEventCreate(&e0));
+            RBF_CUDA(cudaEventCreate(&e1));
+            RBF_CUDA(cudaEventRecord(e0, pb.st));
+            pb.idx.alloc((size_t)n_prog * pb.n);
+            rbf::build_stencils(pb.x.p, pb.z.p, n_all, n_prog, pb.n, 0.0, pb.idx.p, pb.st);
+            pb.ops = {RBF_OP_DX, RBF_OP_DZ};
+            if (pb.hv_k > 0) pb.ops.push_back(RBF_OP_HV);
+            pb.w64.alloc(pb.ops.size() * (size_t)n_prog * pb.n);
+            rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, 0.0, pb.p, pb.l, 0, pb.ops.data(), 2, pb.w64.p,
+                               pb.st);
+            if (pb.hv_k > 0) {
+                int hv = RBF_OP_HV;
+                rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, 0.0, pb.hv_p, pb.l, pb.hv_k, &hv, 1,
+                                   pb.w64.p + 2 * (size_t)n_prog * pb.n, pb.st);
+            }
+            RBF_CUDA(cudaEventRecord(e1, pb.st));
+            RBF_CUDA(cudaEventSynchronize(e1));
+            RBF_CUDA(cudaEventElapsedTime(&pb.weight_build_ms, e0, e1));
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            rbf::choose_threads(pb, 0);
+            rbf::alloc_scratch(pb);
+            RBF_CUDA(cudaStreamSynchronize(pb.st));
+            *out = h;
+        } catch (...) {
+            delete h;
+            throw;
+        }
+    });
+}
+
+int rbf_rhs(rbf_problem *h, double t, void *U, void *dUdt) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h && U && dUdt, "null argument");
+        rbf::enqueue_rhs(h->impl, t, U, dUdt, h->impl.st);
+    });
+}
+
+int rbf_rk4_step(rbf_problem *h, double t, double dt, void *U) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h && U, "null argument");
+        RBF_REQUIRE(std::isfinite(dt) && std::isfinite(t), "non-finite time or step");
+        rbf::enqueue_rk4_step(h->impl, t, dt, U, h->impl.st, false, 0);
+    });
+}
+
+int rbf_run(rbf_problem *h, double t0, double dt, int64_t n_steps, void *U) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h, "null problem");
+        rbf::run(h->impl, t0, dt, n_steps, U);
+    });
+}
+
+int rbf_run_host(rbf_problem *h, double t0, double dt, int64_t n_steps, void *U_host) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h && U_host, "null argument");
+        Problem &pb = h->impl;
+        const int64_t stride = pb.kind == rbf::kNS ? pb.n_all : pb.n_prog;
+        const size_t bytes = (size_t)pb.F * stride * pb.tsize();
+        // the problem keeps one device copy of the state for repeated calls
+        if (pb.host_state.bytes() < bytes) pb.host_state.alloc(bytes);
+        RBF_CUDA(cudaMemcpyAsync(pb.host_state.p, U_host, bytes, cudaMemcpyHostToDevice, pb.st));
+        rbf::run(pb, t0, dt, n_steps, pb.host_state.p);
+        RBF_CUDA(cudaMemcpyAsync(U_host, pb.host_state.p, bytes, cudaMemcpyDeviceToHost, pb.st));
+        RBF_CUDA(cudaStreamSynchronize(pb.st));
+    });
+}
+
+int rbf_sync(rbf_problem *h) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h, "null problem");
+        RBF_CUDA(cudaStreamSynchronize(h->impl.st));
+        RBF_CUDA(cudaStreamSynchronize(h->impl.cap));
+    });
+}
+
+int rbf_minmax(rbf_problem *h, const void *U, double *out) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h && U && out, "null argument");
+        rbf::minmax(h->impl, U, out);
+    });
+}
+
+int rbf_get_info(const rbf_problem *h, rbf_info *out) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h && out, "null argument");
+        const Problem &pb = h->impl;
+        memset(out, 0, sizeof(*out));
+        out->n_prog = pb.n_prog;
+        out->n_all = pb.n_all;
+        out->n_ghost = pb.gh.n_ghost;
+        out->n_fields = pb.F;
+        out->precision = pb.precision;
+        out->n_sten = pb.n;
+        out->threads_per_node = pb.G;
+        out->slots = pb.SL * pb.G;
+        const bool ghosts = pb.kind == rbf::kNS && pb.gh.n_ghost > 0;
+        out->launches_per_step = 4 * (ghosts ? 3 : 1) + (pb.kind == rbf::kAdvection ? 1 : 0);
+        out->n_components = pb.gh.n_comp;
+        out->n_ghost_classes = pb.gh.n_class;
+        out->weight_build_ms = pb.weight_build_ms;
+        out->ghost_setup_ms = pb.ghost_setup_ms;
+        const double ts = (double)pb.tsize();
+        const double slots = pb.n_slots;   // algorithmic, without padding
+        if (pb.kind == rbf::kNS) {
+            // packed weights (4 operators) + index per slot, the node's own
+            // values, U_n, the RK4 accumulator read+write, the stage output,
+            // pibar and the flag byte
+            out->rhs_bytes_per_node = slots * (4 * ts + 4) + 4 * ts + 4 * ts + 8 * ts + 4 * ts + ts + 1;
+            out->rhs_flops_per_node = slots * (12 * 2 + (pb.diff ? 4 : 0)) + 40 + 4 * 4;
+        } else {
+            out->rhs_bytes_per_node = slots * (2 * ts + 4) + ts + ts + 2 * ts + ts;
+            out->rhs_flops_per_node = slots * 4 + 10;
+        }
+    });
+}
+
+int rbf_get_weights(const rbf_problem *h, int32_t op, double *out, int32_t *out_idx) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h && out, "null argument");
+        const Problem &pb = h->impl;
+        int slot = -1;
+        for (size_t i = 0; i < pb.ops.size(); ++i)
+            if (pb.ops[i] == op) slot = (int)i;
+        RBF_REQUIRE(slot >= 0, "operator %d not built for this problem", op);
+        const size_t cnt = (size_t)pb.n_prog * pb.n;
+        RBF_CUDA(cudaMemcpy(out, pb.w64.p + slot * cnt, cnt * 8, cudaMemcpyDeviceToHost));
+        if (out_idx) RBF_CUDA(cudaMemcpy(out_idx, pb.idx.p, cnt * 4, cudaMemcpyDeviceToHost));
+    });
+}
+
+int rbf_destroy(rbf_problem *h) {
+    return rbf::guarded([&] {
+        if (!h) return;
+        cudaStreamSynchronize(h->impl.st);
+        cudaStreamSynchronize(h->impl.cap);
+        delete h;
+    });
+}
+
+// Kernel timing for measurement: when enabled, rbf_run captures one step per
+// graph with timing events around the four fused stage kernels; afterwards
+// rbf_stage_kernel_ms returns their summed device time of the last step.
+int rbf_set_stage_timing(rbf_problem *h, int32_t enable) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h, "null problem");
+        h->impl.record_rhs_events = enable != 0;
+        rbf::invalidate_graph(h->impl);
+    });
+}
+
+int rbf_stage_kernel_ms(rbf_problem *h, double *ms) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h && ms, "null argument");
+        Problem &pb = h->impl;
+        RBF_REQUIRE(pb.record_rhs_events && !pb.rhs_ev.empty(), "stage timing not enabled or no step run");
+        RBF_CUDA(cudaStreamSynchronize(pb.cap));
+        double total = 0.0;
+        for (size_t q = 0; q + 1 < pb.rhs_ev.size(); q += 2) {
+            float t = 0.f;
+            RBF_CUDA(cudaEventElapsedTime(&t, pb.rhs_ev[q], pb.rhs_ev[q + 1]));
+            total += t;
+        }
+        *ms = total;
+    });
+}
+
+}  // extern "C"

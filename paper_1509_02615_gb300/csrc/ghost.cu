@@ -1,0 +1,426 @@
+// a4: ghost nodes (Sec. 5.2, Eq. (bcEqn)).
+//
+// Each wall node gets one ghost outside the domain; the ghost values follow
+// from enforcing the boundary conditions at all wall nodes at once:
+//     W_G u_G = b - W_I u_I - W_B u_B.
+// Setup: the ghosts are split into independent systems (connected components
+// of the ghost-coupling graph, e.g. the top and the bottom wall); for every
+// component and every distinct boundary-operator pattern the dense W_G block
+// is inverted once by Gauss-Jordan elimination with partial pivoting (FP64,
+// one launch pair per pivot, all blocks batched).
+// Every RK stage: (1) one thread per (field, wall row) forms the residual
+// r = b - W_I u_I - W_B u_B from the row's stencil; (2) one warp per
+// (field, ghost) forms u_G = W_G^{-1} r as a dense dot product within its
+// component.  Both kernels are tiny next to the right-hand side; the dense
+// inverse trades a few MB of L2-resident reads for a fully parallel solve.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <numeric>
+
+#include "problem.cuh"
+
+namespace rbf {
+
+namespace {
+
+// operator of each field's boundary condition: [wall kind][field]
+// bottom/top (Sec. 6.3): u_z, w_zz, theta'_z, pi'_z; left/right (Sec. 6.4):
+// u_xx, w_x, theta'_x, pi'_x.
+const int kBcOps[2][4] = {{RBF_OP_DZ, RBF_OP_DZZ, RBF_OP_DZ, RBF_OP_DZ},
+                          {RBF_OP_DXX, RBF_OP_DX, RBF_OP_DX, RBF_OP_DX}};
+
+__global__ void gather_rows(const int32_t *idx, const double *w64, int nops, int64_t n_prog, int n,
+                            const int32_t *owner, int64_t ng, int32_t *ridx, double *rw) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ng * n) return;
+    int64_t r = t / n;
+    int k = (int)(t - r * n);
+    int64_t b = owner[r];
+    ridx[r * n + k] = idx[b * n + k];
+    for (int o = 0; o < nops; ++o) rw[(o * ng + r) * n + k] = w64[((int64_t)o * n_prog + b) * n + k];
+}
+
+__global__ void gj_pivot(double *A, double *B, const int *msize, const int64_t *moff, const double *tol,
+                         int k, double *colk, int maxm, int *bad) {
+    const int mi = blockIdx.x;
+    const int m = msize[mi];
+    if (k >= m) return;
+    double *a = A + moff[mi], *b = B + moff[mi];
+    double *col = colk + (int64_t)mi * maxm;
+    __shared__ double bv[256];
+    __shared__ int bi[256];
+    double best = -1.0;
+    int besti = k;
+    for (int i = k + threadIdx.x; i < m; i += blockDim.x) {
+        double v = fabs(a[(int64_t)i * m + k]);
+        if (v > best) { best = v; besti = i; }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = besti;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            double ov = bv[threadIdx.x + s];
+            int oi = bi[threadIdx.x + s];
+            if (ov > bv[threadIdx.x] || (ov == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
+                bv[threadIdx.x] = ov;
+                bi[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    const int p = bi[0];
+    if (!(bv[0] > tol[mi])) {
+        if (threadIdx.x == 0) atomicExch(bad, mi + 1);
+        return;
+    }
+    if (p != k) {
+        for (int j = threadIdx.x; j < m; j += blockDim.x) {
+            double t = a[(int64_t)k * m + j];
+            a[(int64_t)k * m + j] = a[(int64_t)p * m + j];
+            a[(int64_t)p * m + j] = t;
+            t = b[(int64_t)k * m + j];
+            b[(int64_t)k * m + j] = b[(int64_t)p * m + j];
+            b[(int64_t)p * m + j] = t;
+        }
+    }
+    __syncthreads();
+    const double inv = 1.0 / a[(int64_t)k * m + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+        a[(int64_t)k * m + j] *= inv;
+        b[(int64_t)k * m + j] *= inv;
+    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) col[i] = (i == k) ? 0.0 : a[(int64_t)i * m + k];
+}
+
+__global__ void gj_eliminate(double *A, double *B, const int *msize, const int64_t *moff, int k,
+                             const double *colk, int maxm) {
+    const int mi = blockIdx.z;
+    const int m = msize[mi];
+    const int i = blockIdx.y;
+    if (k >= m || i >= m || i == k) return;
+    double f = colk[(int64_t)mi * maxm + i];
+    if (f == 0.0) return;
+    double *a = A + moff[mi], *b = B + moff[mi];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < 2 * m; j += gridDim.x * blockDim.x) {
+        if (j < m) {
+            if (j > k) a[(int64_t)i * m + j] -= f * a[(int64_t)k * m + j];
+        } else {
+            int jj = j - m;
+            b[(int64_t)i * m + jj] -= f * b[(int64_t)k * m + jj];
+        }
+    }
+}
+
+template <class T>
+__global__ void to_t(const double *src, T *dst, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (T)src[i];
+}
+
+// r[f][pos(r)] = b_f(r) - sum over the row's non-ghost stencil nodes
+template <class T>
+__global__ void ghost_residual(const T *__restrict__ U, int64_t n_all, int64_t ng, int n,
+                               const int32_t *__restrict__ gidx, const T *__restrict__ gw,
+                               const int32_t *__restrict__ owner, const unsigned char *__restrict__ tb,
+                               const int32_t *__restrict__ pos, T *__restrict__ res, T cp_tb2, T theta_bar,
+                               T gconst) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= 4 * ng) return;
+    int f = (int)(t / ng);
+    int64_t r = t - f * ng;
+    const T *u = U + f * n_all;
+    const T *w = gw + (int64_t)f * n * ng;
+    T acc = 0;
+    for (int k = 0; k < n; ++k) acc += w[k * ng + r] * u[gidx[k * ng + r]];
+    T b = 0;
+    if (f == 3 && tb[r]) {
+        // pi'_z = g theta' / (c_p theta_bar (theta_bar + theta')) at the wall node
+        T th = U[2 * n_all + owner[r]];
+        b = gconst * th / (cp_tb2 + cp_tb2 / theta_bar * th);
+    }
+    res[f * ng + pos[r]] = b - acc;
+}
+
+// u_G = W_G^{-1} r within each component: one warp per (field, position)
+template <class T>
+__global__ void ghost_apply(T *__restrict__ U, int64_t n_all, int64_t n_prog, int64_t ng,
+                            const int32_t *__restrict__ comp_of, const int64_t *__restrict__ comp_start,
+                            const int64_t *__restrict__ inv_off, int n_comp, const T *__restrict__ inv,
+                            const T *__restrict__ res, const int32_t *__restrict__ at, int4 fclass) {
+    int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int lane = threadIdx.x & 31;
+    if (wid >= 4 * ng) return;
+    int f = (int)(wid / ng);
+    int64_t q = wid - f * ng;
+    int c = comp_of[q];
+    int64_t s0 = comp_start[c];
+    int m = (int)(comp_start[c + 1] - s0);
+    int row = (int)(q - s0);
+    int cls = f == 0 ? fclass.x : f == 1 ? fclass.y : f == 2 ? fclass.z : fclass.w;
+    const T *Ainv = inv + inv_off[cls * n_comp + c] + (int64_t)row * m;
+    const T *rr = res + f * ng + s0;
+    T acc = 0;
+    for (int j = lane; j < m; j += 32) acc += Ainv[j] * rr[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) U[f * n_all + n_prog + at[q]] = acc;
+}
+
+struct UnionFind {
+    std::vector<int64_t> p;
+    explicit UnionFind(int64_t n) : p(n) { std::iota(p.begin(), p.end(), 0); }
+    int64_t find(int64_t a) {
+        while (p[a] != a) a = p[a] = p[p[a]];
+        return a;
+    }
+    void unite(int64_t a, int64_t b) {
+        a = find(a);
+        b = find(b);
+        if (a != b) p[std::max(a, b)] = std::min(a, b);
+    }
+};
+
+}  // namespace
+
+void build_ghost_plan(Problem &pb, const int32_t *kind_host, const int32_t *owner_host) {
+    GhostPlan &gh = pb.gh;
+    const int64_t ng = pb.n_all - pb.n_prog;
+    gh.n_ghost = ng;
+    if (ng == 0) return;
+    const int n = pb.n;
+    cudaStream_t st = pb.st;
+    cudaEvent_t e0, e1;
+    RBF_CUDA(cudaEventCreate(&e0));
+    RBF_CUDA(cudaEventCreate(&e1));
+    RBF_CUDA(cudaEventRecord(e0, st));
+
+    // operator index of each BC op within pb.ops
+    auto op_slot = [&](int op) {
+        for (size_t i = 0; i < pb.ops.size(); ++i)
+            if (pb.ops[i] == op) return (int)i;
+        RBF_FAIL(RBF_E_ARG, "boundary operator %d was not built", op);
+    };
+    for (int64_t r = 0; r < ng; ++r) {
+        int64_t b = owner_host[r];
+        RBF_REQUIRE(b >= 0 && b < pb.n_prog, "ghost_owner[%lld]=%lld out of range", (long long)r, (long long)b);
+        RBF_REQUIRE(kind_host[b] >= 1 && kind_host[b] <= 4, "ghost %lld is owned by a non-wall node %lld",
+                    (long long)r, (long long)b);
+    }
+    DevBuf<int32_t> owner(ng), ridx(ng * n);
+    const int nops = (int)pb.ops.size();
+    DevBuf<double> rw((size_t)nops * ng * n);
+    RBF_CUDA(cudaMemcpyAsync(owner.p, owner_host, ng * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    gather_rows<<<div_up(ng * n, 256), 256, 0, st>>>(pb.idx.p, pb.w64.p, nops, pb.n_prog, n, owner.p, ng, ridx.p, rw.p);
+    RBF_CHECK_LAUNCH();
+    std::vector<int32_t> hidx(ng * n);
+    std::vector<double> hw((size_t)nops * ng * n);
+    RBF_CUDA(cudaMemcpyAsync(hidx.data(), ridx.p, ridx.bytes(), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(cudaMemcpyAsync(hw.data(), rw.p, rw.bytes(), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(cudaStreamSynchronize(st));
+
+    // components of the ghost coupling graph
+    UnionFind uf(ng);
+    std::vector<char> seen(ng, 0);
+    for (int64_t r = 0; r < ng; ++r) {
+        bool any = false;
+        for (int k = 0; k < n; ++k) {
+            int64_t j = hidx[r * n + k];
+            if (j >= pb.n_prog) {
+                uf.unite(r, j - pb.n_prog);
+                seen[j - pb.n_prog] = 1;
+                any = true;
+            }
+        }
+        if (!any) RBF_FAIL(RBF_E_SINGULAR, "wall node %d has no ghost in its stencil", owner_host[r]);
+    }
+    for (int64_t g = 0; g < ng; ++g)
+        if (!seen[g]) RBF_FAIL(RBF_E_SINGULAR, "ghost %lld lies in no wall node's stencil", (long long)(pb.n_prog + g));
+    std::map<int64_t, int> comp_id;
+    std::vector<int> comp(ng);
+    for (int64_t r = 0; r < ng; ++r) {
+        int64_t root = uf.find(r);
+        auto it = comp_id.find(root);
+        if (it == comp_id.end()) it = comp_id.emplace(root, (int)comp_id.size()).first;
+        comp[r] = it->second;
+    }
+    const int nc = (int)comp_id.size();
+    std::vector<int32_t> at(ng), pos(ng), comp_of(ng);
+    std::vector<int64_t> cstart(nc + 1, 0);
+    for (int64_t r = 0; r < ng; ++r) cstart[comp[r] + 1]++;
+    for (int c = 0; c < nc; ++c) cstart[c + 1] += cstart[c];
+    {
+        std::vector<int64_t> fill(cstart.begin(), cstart.end() - 1);
+        for (int64_t r = 0; r < ng; ++r) {
+            int64_t q = fill[comp[r]]++;
+            at[q] = (int32_t)r;
+            pos[r] = (int32_t)q;
+            comp_of[q] = comp[r];
+        }
+    }
+    // boundary operator of each (row, field); fields with equal patterns share a class
+    std::vector<int> wall(ng);
+    for (int64_t r = 0; r < ng; ++r) {
+        int kd = kind_host[owner_host[r]];
+        wall[r] = (kd == 1 || kd == 2) ? 0 : 1;
+    }
+    std::vector<std::vector<int>> patterns;
+    for (int f = 0; f < 4; ++f) {
+        std::vector<int> pat(ng);
+        for (int64_t r = 0; r < ng; ++r) pat[r] = kBcOps[wall[r]][f];
+        int cls = -1;
+        for (size_t c = 0; c < patterns.size(); ++c)
+            if (patterns[c] == pat) cls = (int)c;
+        if (cls < 0) {
+            cls = (int)patterns.size();
+            patterns.push_back(pat);
+        }
+        gh.field_class[f] = cls;
+    }
+    const int ncl = (int)patterns.size();
+    gh.n_comp = nc;
+    gh.n_class = ncl;
+
+    // dense W_G blocks, one per (class, component)
+    std::vector<int> msize;
+    std::vector<int64_t> moff;
+    std::vector<double> tol;
+    int64_t total = 0;
+    int maxm = 0;
+    for (int cl = 0; cl < ncl; ++cl)
+        for (int c = 0; c < nc; ++c) {
+            int m = (int)(cstart[c + 1] - cstart[c]);
+            msize.push_back(m);
+            moff.push_back(total);
+            total += (int64_t)m * m;
+            maxm = std::max(maxm, m);
+        }
+    RBF_REQUIRE(total < ((int64_t)1 << 31), "ghost systems too large (%lld entries)", (long long)total);
+    std::vector<double> hA(total, 0.0);
+    for (int cl = 0; cl < ncl; ++cl)
+        for (int c = 0; c < nc; ++c) {
+            int mi = cl * nc + c;
+            int m = msize[mi];
+            double amax = 0.0;
+            for (int64_t q = cstart[c]; q < cstart[c + 1]; ++q) {
+                int64_t r = at[q];
+                int slot = op_slot(patterns[cl][r]);
+                for (int k = 0; k < n; ++k) {
+                    int64_t j = hidx[r * n + k];
+                    if (j < pb.n_prog) continue;
+                    int64_t col = pos[j - pb.n_prog] - cstart[c];
+                    double v = hw[((size_t)slot * ng + r) * n + k];
+                    hA[moff[mi] + (q - cstart[c]) * m + col] += v;
+                    amax = std::max(amax, std::fabs(v));
+                }
+            }
+            tol.push_back(1e-13 * amax);
+        }
+    const int nm = (int)msize.size();
+    DevBuf<double> dA(total), dB(total), dcol((size_t)nm * maxm), dtol(nm);
+    DevBuf<int> dms(nm), dbad(1);
+    DevBuf<int64_t> dmo(nm);
+    std::vector<double> hB(total, 0.0);
+    for (int mi = 0; mi < nm; ++mi)
+        for (int i = 0; i < msize[mi]; ++i) hB[moff[mi] + (int64_t)i * msize[mi] + i] = 1.0;
+    RBF_CUDA(cudaMemcpyAsync(dA.p, hA.data(), dA.bytes(), cudaMemcpyHostToDevice, st));
+    RBF_CUDA(cudaMemcpyAsync(dB.p, hB.data(), dB.bytes(), cudaMemcpyHostToDevice, st));
+    RBF_CUDA(cudaMemcpyAsync(dms.p, msize.data(), nm * sizeof(int), cudaMemcpyHostToDevice, st));
+    RBF_CUDA(cudaMemcpyAsync(dmo.p, moff.data(), nm * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    RBF_CUDA(cudaMemcpyAsync(dtol.p, tol.data(), nm * sizeof(double), cudaMemcpyHostToDevice, st));
+    RBF_CUDA(cudaMemsetAsync(dbad.p, 0, sizeof(int), st));
+    for (int k = 0; k < maxm; ++k) {
+        gj_pivot<<<nm, 256, 0, st>>>(dA.p, dB.p, dms.p, dmo.p, dtol.p, k, dcol.p, maxm, dbad.p);
+        dim3 grid(div_up(2 * maxm, 256) > 4 ? 4 : div_up(2 * maxm, 256), maxm, nm);
+        gj_eliminate<<<grid, 256, 0, st>>>(dA.p, dB.p, dms.p, dmo.p, k, dcol.p, maxm);
+    }
+    RBF_CHECK_LAUNCH();
+    int hbad = 0;
+    RBF_CUDA(cudaMemcpyAsync(&hbad, dbad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(cudaStreamSynchronize(st));
+    if (hbad) RBF_FAIL(RBF_E_SINGULAR, "ghost system %d (class %d, component %d) is singular", hbad - 1,
+                       (hbad - 1) / nc, (hbad - 1) % nc);
+
+    const size_t ts = pb.tsize();
+    gh.inv.alloc(total * ts);
+    if (pb.precision == 64)
+        RBF_CUDA(cudaMemcpyAsync(gh.inv.p, dB.p, dB.bytes(), cudaMemcpyDeviceToDevice, st));
+    else
+        to_t<float><<<div_up(total, 256), 256, 0, st>>>(dB.p, (float *)gh.inv.p, total);
+    RBF_CHECK_LAUNCH();
+
+    // per-row residual operators: BC weights with the ghost entries zeroed
+    std::vector<double> gwd((size_t)4 * n * ng, 0.0);
+    std::vector<int32_t> gidx((size_t)n * ng);
+    std::vector<unsigned char> tbv(ng);
+    for (int64_t r = 0; r < ng; ++r) {
+        tbv[r] = wall[r] == 0;
+        for (int k = 0; k < n; ++k) {
+            int64_t j = hidx[r * n + k];
+            bool ghost = j >= pb.n_prog;
+            gidx[(size_t)k * ng + r] = ghost ? owner_host[r] : (int32_t)j;
+            for (int f = 0; f < 4; ++f) {
+                int slot = op_slot(kBcOps[wall[r]][f]);
+                gwd[((size_t)f * n + k) * ng + r] = ghost ? 0.0 : hw[((size_t)slot * ng + r) * n + k];
+            }
+        }
+    }
+    gh.gidx.alloc((size_t)n * ng);
+    gh.gw.alloc((size_t)4 * n * ng * ts);
+    gh.owner.alloc(ng);
+    gh.tb.alloc(ng);
+    gh.pos.alloc(ng);
+    gh.at.alloc(ng);
+    gh.comp_of.alloc(ng);
+    gh.comp_start.alloc(nc + 1);
+    gh.inv_off.alloc(nm);
+    gh.res.alloc((size_t)4 * ng * ts);
+    RBF_CUDA(cudaMemcpyAsync(gh.gidx.p, gidx.data(), gh.gidx.bytes(), cudaMemcpyHostToDevice, st));
+    if (pb.precision == 64) {
+        RBF_CUDA(cudaMemcpyAsync(gh.gw.p, gwd.data(), gwd.size() * 8, cudaMemcpyHostToDevice, st));
+    } else {
+        std::vector<float> gwf(gwd.begin(), gwd.end());
+        RBF_CUDA(cudaMemcpyAsync(gh.gw.p, gwf.data(), gwf.size() * 4, cudaMemcpyHostToDevice, st));
+        RBF_CUDA(cudaStreamSynchronize(st));
+    }
+    RBF_CUDA(cudaMemcpyAsync(gh.owner.p, owner_host, ng * 4, cudaMemcpyHostToDevice, st));
+    RBF_CUDA(cudaMemcpyAsync(gh.tb.p, tbv.data(), ng, cudaMemcpyHostToDevice, st));
+    RBF_CUDA(cudaMemcpyAsync(gh.pos.p, pos.data(), ng * 4, cudaMemcpyHostToDevice, st));
+    RBF_CUDA(cudaMemcpyAsync(gh.at.p, at.data(), ng * 4, cudaMemcpyHostToDevice, st));
+    RBF_CUDA(cudaMemcpyAsync(gh.comp_of.p, comp_of.data(), ng * 4, cudaMemcpyHostToDevice, st));
+    RBF_CUDA(cudaMemcpyAsync(gh.comp_start.p, cstart.data(), (nc + 1) * 8, cudaMemcpyHostToDevice, st));
+    RBF_CUDA(cudaMemcpyAsync(gh.inv_off.p, moff.data(), nm * 8, cudaMemcpyHostToDevice, st));
+    RBF_CUDA(cudaEventRecord(e1, st));
+    RBF_CUDA(cudaStreamSynchronize(st));
+    RBF_CUDA(cudaEventElapsedTime(&pb.ghost_setup_ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
+void enqueue_ghost_fill(Problem &pb, void *U, cudaStream_t s) {
+    GhostPlan &gh = pb.gh;
+    const int64_t ng = gh.n_ghost;
+    if (ng == 0) return;
+    const int n = pb.n;
+    int4 fc = make_int4(gh.field_class[0], gh.field_class[1], gh.field_class[2], gh.field_class[3]);
+    if (pb.precision == 64) {
+        ghost_residual<double><<<div_up(4 * ng, 128), 128, 0, s>>>(
+            (const double *)U, pb.n_all, ng, n, gh.gidx.p, (const double *)gh.gw.p, gh.owner.p, gh.tb.p,
+            gh.pos.p, (double *)gh.res.p, pb.cp * pb.theta_bar * pb.theta_bar, pb.theta_bar, pb.g);
+        ghost_apply<double><<<div_up(4 * ng * 32, 256), 256, 0, s>>>(
+            (double *)U, pb.n_all, pb.n_prog, ng, gh.comp_of.p, gh.comp_start.p, gh.inv_off.p, gh.n_comp,
+            (const double *)gh.inv.p, (const double *)gh.res.p, gh.at.p, fc);
+    } else {
+        ghost_residual<float><<<div_up(4 * ng, 128), 128, 0, s>>>(
+            (const float *)U, pb.n_all, ng, n, gh.gidx.p, (const float *)gh.gw.p, gh.owner.p, gh.tb.p,
+            gh.pos.p, (float *)gh.res.p, (float)(pb.cp * pb.theta_bar * pb.theta_bar), (float)pb.theta_bar,
+            (float)pb.g);
+        ghost_apply<float><<<div_up(4 * ng * 32, 256), 256, 0, s>>>(
+            (float *)U, pb.n_all, pb.n_prog, ng, gh.comp_of.p, gh.comp_start.p, gh.inv_off.p, gh.n_comp,
+            (const float *)gh.inv.p, (const float *)gh.res.p, gh.at.p, fc);
+    }
+    RBF_CHECK_LAUNCH();
+}
+
+}  // namespace rbf

@@ -1,0 +1,101 @@
+// Internal layout of an rbf_problem: the packed operators, ghost systems, RK4
+// scratch and captured graphs of one Navier-Stokes or advection problem.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace rbf {
+
+enum ProblemKind { kNS = 0, kAdvection = 1 };
+
+struct GhostPlan {
+    int64_t n_ghost = 0;
+    int n_comp = 0;
+    int n_class = 0;
+    int field_class[4] = {0, 0, 0, 0};
+    DevBuf<int32_t> gidx;        // [n][n_ghost] owner-stencil node per slot
+    DevBuf<unsigned char> gw;    // [F][n][n_ghost] T: BC weights, zero on ghosts
+    DevBuf<int32_t> owner;       // [n_ghost]
+    DevBuf<unsigned char> tb;    // [n_ghost] 1 if the owner is a bottom/top node
+    DevBuf<int32_t> pos;         // [n_ghost] position of ghost row in component order
+    DevBuf<int32_t> at;          // [n_ghost] ghost row at each position
+    DevBuf<int32_t> comp_of;     // [n_ghost] component of each position
+    DevBuf<int64_t> comp_start;  // [n_comp + 1] first position of each component
+    DevBuf<int64_t> inv_off;     // [n_class][n_comp] offset of each inverse block
+    DevBuf<unsigned char> inv;   // T [sum over class, comp of m^2]
+    DevBuf<unsigned char> res;   // T [F][n_ghost] residual b - W_I u_I - W_B u_B
+};
+
+struct Problem {
+    ProblemKind kind = kNS;
+    cudaStream_t st = nullptr;    // caller's stream
+    cudaStream_t cap = nullptr;   // private stream for graph capture
+    int precision = 64;
+    int F = 4;
+    int64_t n_prog = 0, n_all = 0;
+    int n = 0;                    // stencil size
+    int G = 4;                    // threads per node
+    int diff = 0;                 // 1: difference form (self slot dropped)
+    int n_slots = 0;              // neighbour slots per node before padding
+    int SL = 0;                   // slots per lane
+    // NS physics
+    double mu = 0, gamma = 0, hvc = 0, theta_bar = 300, g = 9.81, cp = 1004, cv = 717, rd = 287;
+    double period_x = 0;
+    int p = 7, l = 4, hv_k = 0, hv_p = 7;
+    // advection
+    double period_T = 1.0;
+    DevBuf<double> vel;           // [2][n_all] spatial velocity factors U, V
+    DevBuf<int32_t> src;          // [n_all] source node of each node
+
+    // FP64 setup products (kept for rbf_get_weights)
+    std::vector<int> ops;         // operator code of each weight block
+    DevBuf<double> x, z;
+    DevBuf<int32_t> idx;          // [n_prog][n]
+    DevBuf<double> w64;           // [ops][n_prog][n]
+
+    // packed operators, precision T
+    int n_packed = 4;
+    DevBuf<int32_t> pidx;         // [SL][n_prog][G]
+    DevBuf<unsigned char> pw;     // T [n_packed][SL][n_prog][G]
+    DevBuf<unsigned char> pibar;  // T [n_prog]
+    DevBuf<unsigned char> flags;  // [n_prog]: bit0 w Dirichlet, bit1 u Dirichlet
+
+    GhostPlan gh;
+
+    // RK4 scratch, precision T
+    DevBuf<unsigned char> S0, S1, K;
+    DevBuf<double> tdev;          // device time for graph replays (advection)
+    DevBuf<unsigned char> host_state;  // device copy used by rbf_run_host
+
+    // graph cache
+    cudaGraphExec_t graph = nullptr;
+    void *graph_U = nullptr;
+    double graph_dt = 0.0;
+    int graph_steps = 0;
+    bool record_rhs_events = false;
+    std::vector<cudaEvent_t> rhs_ev;   // [2 * 4 * graph_steps] when recording
+
+    float weight_build_ms = 0.f, ghost_setup_ms = 0.f;
+
+    size_t tsize() const { return precision == 64 ? 8 : 4; }
+    ~Problem();
+};
+
+// Launches one RK4 step (4 stages, ghost fill before each) on stream s.
+void enqueue_rk4_step(Problem &pb, double t, double dt, void *U, cudaStream_t s, bool record_events, int step_in_graph);
+void enqueue_rhs(Problem &pb, double t, void *U, void *dUdt, cudaStream_t s);
+void autotune_threads_per_node(Problem &pb);
+void pack_operators(Problem &pb);
+void build_ghost_plan(Problem &pb, const int32_t *kind_host, const int32_t *owner_host);
+void enqueue_ghost_fill(Problem &pb, void *U, cudaStream_t s);
+void minmax(Problem &pb, const void *U, double *out);
+
+}  // namespace rbf
+
+struct rbf_problem {
+    rbf::Problem impl;
+};

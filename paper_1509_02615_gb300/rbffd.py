@@ -1,0 +1,285 @@
+"""Python binding of librbffd (ctypes): argument marshalling only.
+
+Every step of the method runs in the CUDA library; this module turns torch
+tensors into device pointers and the library's status codes into exceptions.
+There is no CPU fallback: if librbffd.so is missing or no GPU is present,
+every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+from . import inputs as inp
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librbffd.so")
+
+RBF_OK, RBF_E_ARG, RBF_E_SINGULAR, RBF_E_NONFINITE, RBF_E_TIMEOUT, RBF_E_CUDA, RBF_E_OOM = range(7)
+OP = {"dx": 0, "dz": 1, "lap": 2, "hv": 3, "dxx": 4, "dzz": 5}
+
+
+class RBFError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"librbffd error {code}: {msg}")
+        self.code = code
+
+
+class NSParams(C.Structure):
+    _fields_ = [("n_sten", C.c_int32), ("phs_p", C.c_int32), ("poly_l", C.c_int32), ("hv_k", C.c_int32),
+                ("hv_p", C.c_int32), ("precision", C.c_int32), ("threads_per_node", C.c_int32),
+                ("reserved", C.c_int32), ("period_x", C.c_double), ("mu", C.c_double), ("gamma", C.c_double),
+                ("theta_bar", C.c_double), ("g", C.c_double), ("cp", C.c_double), ("cv", C.c_double),
+                ("rd", C.c_double)]
+
+
+class AdvParams(C.Structure):
+    _fields_ = [("n_sten", C.c_int32), ("phs_p", C.c_int32), ("poly_l", C.c_int32), ("hv_k", C.c_int32),
+                ("hv_p", C.c_int32), ("precision", C.c_int32), ("gamma", C.c_double), ("period_T", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_prog", C.c_int64), ("n_all", C.c_int64), ("n_ghost", C.c_int64), ("n_fields", C.c_int32),
+                ("precision", C.c_int32), ("n_sten", C.c_int32), ("threads_per_node", C.c_int32),
+                ("slots", C.c_int32), ("launches_per_step", C.c_int32), ("n_components", C.c_int32),
+                ("n_ghost_classes", C.c_int32), ("weight_build_ms", C.c_double), ("ghost_setup_ms", C.c_double),
+                ("rhs_bytes_per_node", C.c_double), ("rhs_flops_per_node", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/rbffd.h
+_P, _I64, _I32, _D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+SIGNATURES = [
+    ("rbf_last_error", C.c_char_p, []),
+    ("rbf_build_stencils", C.c_int, [_P, _P, _I64, _I64, _I32, _D, _P, _P]),
+    ("rbf_build_weights", C.c_int, [_P, _P, _I64, _P, _I64, _I32, _D, _I32, _I32, _I32, _P, _I32, _P, _P]),
+    ("rbf_ns_create", C.c_int, [C.POINTER(_P), C.POINTER(NSParams), _P, _P, _I64, _I64, _P, _P, _P]),
+    ("rbf_adv_create", C.c_int, [C.POINTER(_P), C.POINTER(AdvParams), _P, _P, _I64, _I64, _P, _P, _P, _P]),
+    ("rbf_rhs", C.c_int, [_P, _D, _P, _P]),
+    ("rbf_rk4_step", C.c_int, [_P, _D, _D, _P]),
+    ("rbf_run", C.c_int, [_P, _D, _D, _I64, _P]),
+    ("rbf_run_host", C.c_int, [_P, _D, _D, _I64, _P]),
+    ("rbf_sync", C.c_int, [_P]),
+    ("rbf_minmax", C.c_int, [_P, _P, _P]),
+    ("rbf_get_info", C.c_int, [_P, C.POINTER(Info)]),
+    ("rbf_get_weights", C.c_int, [_P, _I32, _P, _P]),
+    ("rbf_set_stage_timing", C.c_int, [_P, _I32]),
+    ("rbf_stage_kernel_ms", C.c_int, [_P, C.POINTER(C.c_double)]),
+    ("rbf_destroy", C.c_int, [_P]),
+]
+
+
+def lib():
+    """The loaded librbffd (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1509_02615_gb300._build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code):
+    if code != RBF_OK:
+        raise RBFError(code, lib().rbf_last_error().decode())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("librbffd needs a CUDA GPU; none is available")
+    return torch
+
+
+def _stream():
+    return C.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+# ---- a1, a2: stateless builders ---------------------------------------------------
+
+def build_stencils(x, z, n_centers, n, period_x=0.0):
+    """n nearest nodes of nodes 0..n_centers-1 among all nodes (device tensors)."""
+    torch = _torch()
+    x = x.to(device="cuda", dtype=torch.float64).contiguous()
+    z = z.to(device="cuda", dtype=torch.float64).contiguous()
+    idx = torch.empty((n_centers, n), dtype=torch.int32, device="cuda")
+    _check(lib().rbf_build_stencils(_ptr(x), _ptr(z), x.numel(), n_centers, n, float(period_x), _ptr(idx), _stream()))
+    return idx
+
+
+def build_weights(x, z, idx, p, l, ops, hv_k=0, period_x=0.0):
+    """Weights [len(ops), N, n] (float64, device) of the stencils idx [N, n]."""
+    torch = _torch()
+    x = x.to(device="cuda", dtype=torch.float64).contiguous()
+    z = z.to(device="cuda", dtype=torch.float64).contiguous()
+    idx = idx.to(device="cuda", dtype=torch.int32).contiguous()
+    N, n = idx.shape
+    codes = np.array([OP[o] if isinstance(o, str) else int(o) for o in ops], np.int32)
+    w = torch.empty((len(codes), N, n), dtype=torch.float64, device="cuda")
+    _check(lib().rbf_build_weights(_ptr(x), _ptr(z), x.numel(), _ptr(idx), N, n, float(period_x), p, l, hv_k,
+                                   _host_ptr(codes), len(codes), _ptr(w), _stream()))
+    return w
+
+
+# ---- problems ---------------------------------------------------------------------
+
+class Problem:
+    """A stepping context owned by librbffd (Navier-Stokes or advection)."""
+
+    def __init__(self, handle, n_fields, n_prog, n_all, precision, kind):
+        self._h = handle
+        self.n_fields = n_fields
+        self.n_prog = n_prog
+        self.n_all = n_all
+        self.precision = precision
+        self.kind = kind
+
+    @property
+    def dtype(self):
+        torch = _torch()
+        return torch.float64 if self.precision == 64 else torch.float32
+
+    @property
+    def state_shape(self):
+        return (self.n_fields, self.n_all if self.kind == "ns" else self.n_prog)
+
+    def _state(self, U):
+        torch = _torch()
+        if not (U.is_cuda and U.dtype == self.dtype and U.is_contiguous() and tuple(U.shape) == self.state_shape):
+            raise ValueError(f"state must be a contiguous CUDA {self.dtype} tensor of shape {self.state_shape}")
+        return U
+
+    def rhs(self, t, U, dUdt=None):
+        U = self._state(U)
+        if dUdt is None:
+            dUdt = _torch().empty((self.n_fields, self.n_prog), dtype=self.dtype, device="cuda")
+        _check(lib().rbf_rhs(self._h, float(t), _ptr(U), _ptr(dUdt)))
+        return dUdt
+
+    def rk4_step(self, t, dt, U):
+        _check(lib().rbf_rk4_step(self._h, float(t), float(dt), _ptr(self._state(U))))
+        return U
+
+    def run(self, t0, dt, n_steps, U):
+        _check(lib().rbf_run(self._h, float(t0), float(dt), int(n_steps), _ptr(self._state(U))))
+        return U
+
+    def run_host(self, t0, dt, n_steps, U_host):
+        """End-to-end run on a host (ideally pinned) tensor, copies included."""
+        if U_host.is_cuda or U_host.dtype != self.dtype or tuple(U_host.shape) != self.state_shape:
+            raise ValueError("run_host takes a CPU tensor of the state's dtype and shape")
+        _check(lib().rbf_run_host(self._h, float(t0), float(dt), int(n_steps), C.c_void_p(U_host.data_ptr())))
+        return U_host
+
+    def sync(self):
+        _check(lib().rbf_sync(self._h))
+
+    def minmax(self, U):
+        out = np.zeros((self.n_fields, 2))
+        _check(lib().rbf_minmax(self._h, _ptr(self._state(U)), _host_ptr(out)))
+        return out
+
+    def info(self):
+        i = Info()
+        _check(lib().rbf_get_info(self._h, C.byref(i)))
+        return i.as_dict()
+
+    def weights(self, op):
+        n = self.info()["n_sten"]
+        w = np.zeros((self.n_prog, n))
+        idx = np.zeros((self.n_prog, n), np.int32)
+        _check(lib().rbf_get_weights(self._h, OP[op] if isinstance(op, str) else int(op), _host_ptr(w), _host_ptr(idx)))
+        return w, idx
+
+    def set_stage_timing(self, enable):
+        _check(lib().rbf_set_stage_timing(self._h, 1 if enable else 0))
+
+    def stage_kernel_ms(self):
+        v = C.c_double()
+        _check(lib().rbf_stage_kernel_ms(self._h, C.byref(v)))
+        return v.value
+
+    def close(self):
+        if self._h:
+            _check(lib().rbf_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hyperviscosity_gamma(c, h, k):
+    """gamma = c h^(2k-1): with dt proportional to h this keeps
+    dt * gamma * rho(Delta^k) independent of the resolution (the reading of
+    Sec. 5.3's resolution-independent constant c)."""
+    return c * h ** (2 * k - 1)
+
+
+def ns_problem(nodes: inp.NodeSet, precision=64, n=37, p=7, l=4, hv_k=3, hv_p=None, mu=75.0, gamma=None,
+               gamma_c=2.0 ** -6, threads_per_node=0, theta_bar=inp.THETA_BAR):
+    """Navier-Stokes problem on a node set (Sec. 6.2-6.3 defaults)."""
+    prm = NSParams(n_sten=n, phs_p=p, poly_l=l, hv_k=hv_k, hv_p=hv_p if hv_p else p, precision=precision,
+                   threads_per_node=threads_per_node, reserved=0, period_x=nodes.period_x, mu=mu,
+                   gamma=hyperviscosity_gamma(gamma_c, nodes.h, hv_k) if gamma is None else gamma,
+                   theta_bar=theta_bar, g=inp.G, cp=inp.CP, cv=inp.CV, rd=inp.RD)
+    _torch()
+    h = C.c_void_p()
+    x = np.ascontiguousarray(nodes.x, np.float64)
+    z = np.ascontiguousarray(nodes.z, np.float64)
+    kind = np.ascontiguousarray(nodes.kind, np.int32)
+    owner = np.ascontiguousarray(nodes.ghost_owner, np.int32)
+    _check(lib().rbf_ns_create(C.byref(h), C.byref(prm), _host_ptr(x), _host_ptr(z), nodes.n_prog, nodes.n_all,
+                               _host_ptr(kind), _host_ptr(owner) if owner.size else None, _stream()))
+    pb = Problem(h, 4, nodes.n_prog, nodes.n_all, precision, "ns")
+    pb.params = prm
+    return pb
+
+
+def advection_problem(nodes: inp.NodeSet, precision=64, n=37, p=7, l=4, hv_k=4, hv_p=9, gamma=None,
+                      gamma_c=2.0 ** -14, T=5.0):
+    """Scalar advection in the deformational flow on reflected nodes (Sec. 6.1)."""
+    prm = AdvParams(n_sten=n, phs_p=p, poly_l=l, hv_k=hv_k, hv_p=hv_p, precision=precision,
+                    gamma=hyperviscosity_gamma(gamma_c, nodes.h, hv_k) if gamma is None else gamma, period_T=T)
+    _torch()
+    Uv, Vv = inp.deformational_velocity(nodes.x, nodes.z)
+    Uv = np.ascontiguousarray(Uv, np.float64)
+    Vv = np.ascontiguousarray(Vv, np.float64)
+    x = np.ascontiguousarray(nodes.x, np.float64)
+    z = np.ascontiguousarray(nodes.z, np.float64)
+    src = np.ascontiguousarray(nodes.src, np.int32)
+    h = C.c_void_p()
+    _check(lib().rbf_adv_create(C.byref(h), C.byref(prm), _host_ptr(x), _host_ptr(z), nodes.n_prog, nodes.n_all,
+                                _host_ptr(src), _host_ptr(Uv), _host_ptr(Vv), _stream()))
+    pb = Problem(h, 1, nodes.n_prog, nodes.n_all, precision, "advection")
+    pb.params = prm
+    return pb
+
+
+def state_tensor(U, precision, device="cuda"):
+    """float64 numpy state -> contiguous tensor of the problem's precision."""
+    torch = _torch()
+    return torch.as_tensor(np.ascontiguousarray(U), dtype=torch.float64 if precision == 64 else torch.float32,
+                           device=device).contiguous()

@@ -1,0 +1,60 @@
+"""The C ABI without a GPU: librbffd builds for sm_103a, loads, exports every
+entry point that include/rbffd.h declares, and rejects bad arguments before
+touching the device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1509_02615_gb300 import _build, rbffd
+    _build.build()
+    return rbffd.lib()
+
+
+def _declared():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(rbf_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert "rbf_build_weights" in names and "rbf_rk4_step" in names and "rbf_run" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header():
+    from paper_1509_02615_gb300 import rbffd
+    bound = {s[0] for s in rbffd.SIGNATURES}
+    assert set(_declared()) <= bound
+
+
+def test_argument_errors_need_no_gpu(lib):
+    from paper_1509_02615_gb300 import rbffd
+    # n = 0 is rejected by the argument checks before any CUDA call
+    rc = lib.rbf_build_stencils(None, None, 10, 10, 0, 0.0, None, None)
+    assert rc == rbffd.RBF_E_ARG
+    assert b"stencil size" in lib.rbf_last_error()
+    rc = lib.rbf_build_weights(None, None, 10, None, 5, 37, 0.0, 4, 4, 0, None, 1, None, None)
+    assert rc == rbffd.RBF_E_ARG
+    rc = lib.rbf_rk4_step(None, 0.0, 1.0, None)
+    assert rc == rbffd.RBF_E_ARG
+
+
+def test_struct_layouts_match_header():
+    from paper_1509_02615_gb300 import rbffd
+    # 8 int32 + 8 doubles; 6 int32 + 2 doubles; see include/rbffd.h
+    assert C.sizeof(rbffd.NSParams) == 8 * 4 + 8 * 8
+    assert C.sizeof(rbffd.AdvParams) == 6 * 4 + 2 * 8
+    assert C.sizeof(rbffd.Info) == 3 * 8 + 8 * 4 + 4 * 8
