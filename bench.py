@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--h", type=float, default=100.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--threads-per-node", type=int, default=0, help="0 = autotuned")
+    ap.add_argument("--large-h", type=float, default=25.0,
+                    help="spacing of the HBM-roofline case (0 = skip); its working set exceeds L2")
     return ap.parse_args()
 
 
@@ -133,11 +136,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_problem(h, precision):
+def make_problem(h, precision, tpn=0):
     from paper_1509_02615_gb300 import inputs as inp
     from paper_1509_02615_gb300 import rbffd
     nodes = inp.density_current_nodes(h)
-    pb = rbffd.ns_problem(nodes, precision=precision)
+    pb = rbffd.ns_problem(nodes, precision=precision, threads_per_node=tpn)
     U0 = inp.density_current_state(nodes)
     return nodes, pb, U0
 
@@ -167,6 +170,34 @@ def time_steps(torch, pb, U, dt, steps, warmup, flush, stage_timing):
         t += dt
     pb.set_stage_timing(False)
     return step_ms, stage_ms
+
+
+def large_case(torch, args, flush):
+    """The same density current at a finer spacing, whose FP32 working set is
+    several times larger than L2: the stage kernel's HBM roofline."""
+    from paper_1509_02615_gb300 import rbffd
+    pk, pk_kind = peaks()
+    nodes, pb, U0 = make_problem(args.large_h, 32)
+    info = pb.info()
+    U = rbffd.state_tensor(U0, 32)
+    dt = args.large_h / 400.0
+    steps = 10
+    step_ms, _ = time_steps(torch, pb, U, dt, steps, 3, flush, False)
+    _, stage_ms = time_steps(torch, pb, U, dt, steps, 1, flush, True)
+    avg = float(np.mean(stage_ms)) / 4.0
+    bpl = info["rhs_bytes_per_node"] * nodes.n_prog
+    ach = bpl / (avg / 1e3) / 1e9
+    out = {"workload": f"density current, hexagonal {args.large_h:g} m, {nodes.n_prog} nodes + {nodes.n_ghost} ghosts, FP32",
+           "node_rhs_per_s": 4.0 * nodes.n_prog * steps / (float(sum(step_ms)) / 1e3),
+           "ms_per_step": float(sum(step_ms)) / steps,
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": ach / pk["hbm_gbs"], "traffic": profiled_traffic(f"ns_stage_fp32_hex{int(args.large_h)}"),
+                        "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg,
+                        "peak_source": f"{pk_kind} hbm_gbs"},
+           "threads_per_node": info["threads_per_node"], "prefetch": info["prefetch"],
+           "setup": {"weight_build_ms": info["weight_build_ms"], "ghost_setup_ms": info["ghost_setup_ms"]}}
+    pb.close()
+    return out
 
 
 def cpu_baseline(h, budget_s=12.0):
@@ -228,7 +259,7 @@ def main():
     torch.cuda.set_stream(stream)
     pk, pk_kind = peaks()
 
-    nodes, pb, U0 = make_problem(args.h, args.precision)
+    nodes, pb, U0 = make_problem(args.h, args.precision, args.threads_per_node)
     info = pb.info()
     dt = args.h / 400.0
     U = rbffd.state_tensor(U0, args.precision)
@@ -238,7 +269,11 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        step_ms, stage_ms = time_steps(torch, pb, U, dt, args.steps, args.warmup, flush, True)
+        step_ms, _ = time_steps(torch, pb, U, dt, args.steps, args.warmup, flush, False)
+        torch.cuda.synchronize()
+        # same steps again with timing events around the four stage kernels
+        # (the events also break the programmatic overlap of the launches)
+        _, stage_ms = time_steps(torch, pb, U, dt, args.steps, 1, flush, True)
     torch.cuda.synchronize()
     total_ms = float(sum(step_ms))
     if world > 1:
@@ -257,7 +292,7 @@ def main():
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / pk["hbm_gbs"], "traffic": profiled_traffic(key), "kernel": "ns_stage_kernel",
             "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": stage_avg_ms,
-            "stage_share_of_step": float(np.sum(stage_ms) / total_ms) if stage_ms else None,
+            "stage_share_of_step": float(np.sum(stage_ms) / np.sum(step_ms)) if stage_ms else None,
             "peak_source": f"{pk_kind} hbm_gbs"}
 
     # end to end through the C ABI on a pinned host state, copies included
@@ -290,6 +325,10 @@ def main():
                 "threads_per_node": i64["threads_per_node"]}
         pb64.close()
 
+    large = None
+    if args.large_h > 0:
+        large = large_case(torch, args, flush)
+
     base = None
     if rank == 0 and not args.no_cpu_baseline:
         base = cpu_baseline(args.h)
@@ -303,11 +342,11 @@ def main():
                            "dt_s": dt, "precision": f"fp{args.precision}",
                            "l2": "flushed between timed steps (512 MB write); working set ~31 MB",
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "threads_per_node": info["threads_per_node"]},
+                           "threads_per_node": info["threads_per_node"], "prefetch": info["prefetch"]},
                 "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
                 "gpu_launches": info["launches_per_step"] * args.steps,
                 "setup": {"weight_build_ms": info["weight_build_ms"], "ghost_setup_ms": info["ghost_setup_ms"]},
-                "fp64": fp64, "cpu_baseline": base,
+                "fp64": fp64, "roofline_large": large, "cpu_baseline": base,
                 "state_minmax": {"theta_min": mm[2, 0], "w_min": mm[1, 0], "w_max": mm[1, 1]}}
         print(json.dumps(line), flush=True)
     pb.close()

@@ -101,7 +101,8 @@ typedef struct rbf_ns_params {
     int32_t hv_p;       /* PHS exponent of the Delta^k weights (>= 2k+1)      */
     int32_t precision;  /* 64: FP64 storage and arithmetic; 32: FP64-built
                            weights stored in FP32, FP32 RHS and RK4           */
-    int32_t threads_per_node; /* 0 = autotuned; else 1, 2, 4 or 8             */
+    int32_t threads_per_node; /* 0 = autotuned (lanes per node and register
+                                 prefetch); else 1, 2, 4 or 8 lanes        */
     int32_t reserved;
     double period_x;    /* > 0: periodic in x with this period (m)            */
     double mu;          /* viscosity (m^2/s)                                  */
@@ -193,6 +194,8 @@ typedef struct rbf_info {
     int32_t launches_per_step;  /* kernel launches in one RK4 step          */
     int32_t n_components;       /* independent ghost systems                */
     int32_t n_ghost_classes;    /* distinct ghost matrices per component    */
+    int32_t prefetch;           /* 1: stage kernel holds operands in registers */
+    int32_t reserved;
     double weight_build_ms;     /* GPU time of stencils + weights + pack    */
     double ghost_setup_ms;      /* GPU time of the ghost inverses           */
     double rhs_bytes_per_node;  /* algorithmic HBM bytes of one RHS stage   */

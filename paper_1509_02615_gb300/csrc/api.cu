@@ -87,6 +87,7 @@ void choose_threads(Problem &pb, int requested) {
                     "threads_per_node must be 0, 1, 2, 4 or 8");
         pb.G = requested;
         pack_operators(pb);
+        pb.pf = (pb.kind == kNS && pb.SL <= 10) ? 10 : 0;   // registers hold the operands when they fit
     }
 }
 
@@ -377,6 +378,7 @@ int rbf_get_info(const rbf_problem *h, rbf_info *out) {
         out->launches_per_step = 4 * (ghosts ? 3 : 1) + (pb.kind == rbf::kAdvection ? 1 : 0);
         out->n_components = pb.gh.n_comp;
         out->n_ghost_classes = pb.gh.n_class;
+        out->prefetch = pb.pf > 0 ? 1 : 0;
         out->weight_build_ms = pb.weight_build_ms;
         out->ghost_setup_ms = pb.ghost_setup_ms;
         const double ts = (double)pb.tsize();

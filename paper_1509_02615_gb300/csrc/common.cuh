@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/rbffd.h"
@@ -98,6 +99,30 @@ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // Number of SMs of the current device (cached per call site by callers).
 int sm_count();
+
+// Programmatic dependent launch (sm_90+): a kernel launched with
+// programmatic stream serialization may start while its predecessor is still
+// running.  It must call grid_dep_wait() before touching memory that an
+// earlier kernel writes or reads-after-us; work on constant inputs (weights,
+// indices) can go before the wait.  grid_dep_launch() lets the next kernel
+// be scheduled.  Both are no-ops for ordinary launches.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+void launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, bool pdl, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    RBF_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
 
 // ---- internal entry points shared between translation units ----------------
 // a1: stencils of nodes [0, n_centers) among all n_all (device arrays).

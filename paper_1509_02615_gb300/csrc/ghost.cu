@@ -120,52 +120,117 @@ __global__ void to_t(const double *src, T *dst, int64_t n) {
     if (i < n) dst[i] = (T)src[i];
 }
 
-// r[f][pos(r)] = b_f(r) - sum over the row's non-ghost stencil nodes
+constexpr int kRowLanes = 8;    // lanes per wall row in the residual kernel
+constexpr int kRowPf = 16;      // slots per lane held in registers
+constexpr int kInvPf = 16;      // inverse entries per lane held in registers
+
+// r[f][pos(r)] = b_f(r) - sum over the row's non-ghost stencil nodes, all four
+// fields at once; 8 lanes per row share the stencil slots (layout [row][slot]).
 template <class T>
-__global__ void ghost_residual(const T *__restrict__ U, int64_t n_all, int64_t ng, int n,
-                               const int32_t *__restrict__ gidx, const T *__restrict__ gw,
-                               const int32_t *__restrict__ owner, const unsigned char *__restrict__ tb,
-                               const int32_t *__restrict__ pos, T *__restrict__ res, T cp_tb2, T theta_bar,
-                               T gconst) {
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= 4 * ng) return;
-    int f = (int)(t / ng);
-    int64_t r = t - f * ng;
-    const T *u = U + f * n_all;
-    const T *w = gw + (int64_t)f * n * ng;
-    T acc = 0;
-    for (int k = 0; k < n; ++k) acc += w[k * ng + r] * u[gidx[k * ng + r]];
+__global__ void __launch_bounds__(256) ghost_residual(const T *__restrict__ U, int64_t n_all, int64_t ng, int npad,
+                                                      const int32_t *__restrict__ gidx, const T *__restrict__ gw,
+                                                      const int32_t *__restrict__ owner,
+                                                      const unsigned char *__restrict__ tb,
+                                                      const int32_t *__restrict__ pos, T *__restrict__ res,
+                                                      T cp_tb2, T theta_bar, T gconst) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t r = tid / kRowLanes;
+    const int ln = (int)(tid % kRowLanes);
+    const bool live = r < ng;
+    if (!live) r = ng - 1;
+    const int per = npad / kRowLanes;
+    // constant operands first: they do not depend on the previous kernel
+    int jj[kRowPf];
+    T w0[kRowPf], w1[kRowPf], w2[kRowPf], w3[kRowPf];
+#pragma unroll
+    for (int t = 0; t < kRowPf; ++t) {
+        if (t < per) {
+            const int64_t o = r * npad + ln + kRowLanes * t;
+            jj[t] = __ldg(gidx + o);
+            w0[t] = __ldg(gw + o);
+            w1[t] = __ldg(gw + ng * npad + o);
+            w2[t] = __ldg(gw + 2 * ng * npad + o);
+            w3[t] = __ldg(gw + 3 * ng * npad + o);
+        }
+    }
+    grid_dep_wait();
+    grid_dep_launch();
+    T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+    for (int t = 0; t < kRowPf; ++t) {
+        if (t < per) {
+            const int j = jj[t];
+            a0 += w0[t] * U[j];
+            a1 += w1[t] * U[n_all + j];
+            a2 += w2[t] * U[2 * n_all + j];
+            a3 += w3[t] * U[3 * n_all + j];
+        }
+    }
+#pragma unroll
+    for (int o = kRowLanes / 2; o > 0; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o, kRowLanes);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o, kRowLanes);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o, kRowLanes);
+        a3 += __shfl_xor_sync(0xffffffffu, a3, o, kRowLanes);
+    }
+    if (!live || ln >= 4) return;
+    T acc = ln == 0 ? a0 : ln == 1 ? a1 : ln == 2 ? a2 : a3;
     T b = 0;
-    if (f == 3 && tb[r]) {
+    if (ln == 3 && tb[r]) {
         // pi'_z = g theta' / (c_p theta_bar (theta_bar + theta')) at the wall node
         T th = U[2 * n_all + owner[r]];
         b = gconst * th / (cp_tb2 + cp_tb2 / theta_bar * th);
     }
-    res[f * ng + pos[r]] = b - acc;
+    res[ln * ng + pos[r]] = b - acc;
 }
 
-// u_G = W_G^{-1} r within each component: one warp per (field, position)
+// u_G = W_G^{-1} r within each component: one warp per (class, position)
+// computes every field of that boundary-operator class from one pass over
+// the inverse row (held in registers before the wait).
 template <class T>
-__global__ void ghost_apply(T *__restrict__ U, int64_t n_all, int64_t n_prog, int64_t ng,
-                            const int32_t *__restrict__ comp_of, const int64_t *__restrict__ comp_start,
-                            const int64_t *__restrict__ inv_off, int n_comp, const T *__restrict__ inv,
-                            const T *__restrict__ res, const int32_t *__restrict__ at, int4 fclass) {
-    int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (wid >= 4 * ng) return;
-    int f = (int)(wid / ng);
-    int64_t q = wid - f * ng;
-    int c = comp_of[q];
-    int64_t s0 = comp_start[c];
-    int m = (int)(comp_start[c + 1] - s0);
-    int row = (int)(q - s0);
-    int cls = f == 0 ? fclass.x : f == 1 ? fclass.y : f == 2 ? fclass.z : fclass.w;
+__global__ void __launch_bounds__(256) ghost_apply(T *__restrict__ U, int64_t n_all, int64_t n_prog, int64_t ng,
+                                                   const int32_t *__restrict__ comp_of,
+                                                   const int64_t *__restrict__ comp_start,
+                                                   const int64_t *__restrict__ inv_off, int n_comp, int n_class,
+                                                   const T *__restrict__ inv, const T *__restrict__ res,
+                                                   const int32_t *__restrict__ at, int4 cls_fields) {
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const bool live = wid < (int64_t)n_class * ng;
+    const int64_t w = live ? wid : 0;
+    const int cls = (int)(w / ng);
+    const int64_t q = w - (int64_t)cls * ng;
+    const int c = comp_of[q];
+    const int64_t s0 = comp_start[c];
+    const int m = (int)(comp_start[c + 1] - s0);
+    const int row = (int)(q - s0);
     const T *Ainv = inv + inv_off[cls * n_comp + c] + (int64_t)row * m;
-    const T *rr = res + f * ng + s0;
-    T acc = 0;
-    for (int j = lane; j < m; j += 32) acc += Ainv[j] * rr[j];
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) U[f * n_all + n_prog + at[q]] = acc;
+    T a[kInvPf];
+#pragma unroll
+    for (int t = 0; t < kInvPf; ++t) a[t] = (lane + 32 * t < m) ? __ldg(Ainv + lane + 32 * t) : (T)0;
+    const int fm = cls == 0 ? cls_fields.x : cls == 1 ? cls_fields.y : cls == 2 ? cls_fields.z : cls_fields.w;
+    grid_dep_wait();
+    grid_dep_launch();
+    if (!live) return;
+    T acc[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        if (!(fm & (1 << f))) continue;
+        const T *rr = res + f * ng + s0;
+        T s = 0;
+#pragma unroll
+        for (int t = 0; t < kInvPf; ++t)
+            if (lane + 32 * t < m) s += a[t] * rr[lane + 32 * t];
+        for (int j = lane + 32 * kInvPf; j < m; j += 32) s += __ldg(Ainv + j) * rr[j];
+        acc[f] = s;
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        if (!(fm & (1 << f))) continue;
+        T s = acc[f];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) U[f * n_all + n_prog + at[q]] = s;
+    }
 }
 
 struct UnionFind {
@@ -350,24 +415,28 @@ void build_ghost_plan(Problem &pb, const int32_t *kind_host, const int32_t *owne
         to_t<float><<<div_up(total, 256), 256, 0, st>>>(dB.p, (float *)gh.inv.p, total);
     RBF_CHECK_LAUNCH();
 
-    // per-row residual operators: BC weights with the ghost entries zeroed
-    std::vector<double> gwd((size_t)4 * n * ng, 0.0);
-    std::vector<int32_t> gidx((size_t)n * ng);
+    // per-row residual operators: BC weights with the ghost entries zeroed,
+    // row-major [f][row][slot] with the slots padded to a multiple of 8
+    const int npad = div_up(n, 8) * 8;
+    RBF_REQUIRE(npad <= 8 * 16, "stencil too large for the ghost residual kernel");
+    gh.npad = npad;
+    std::vector<double> gwd((size_t)4 * npad * ng, 0.0);
+    std::vector<int32_t> gidx((size_t)npad * ng);
     std::vector<unsigned char> tbv(ng);
     for (int64_t r = 0; r < ng; ++r) {
         tbv[r] = wall[r] == 0;
-        for (int k = 0; k < n; ++k) {
-            int64_t j = hidx[r * n + k];
+        for (int k = 0; k < npad; ++k) {
+            int64_t j = k < n ? hidx[r * n + k] : pb.n_prog;   // padding acts like a ghost slot
             bool ghost = j >= pb.n_prog;
-            gidx[(size_t)k * ng + r] = ghost ? owner_host[r] : (int32_t)j;
+            gidx[(size_t)r * npad + k] = ghost ? owner_host[r] : (int32_t)j;
             for (int f = 0; f < 4; ++f) {
                 int slot = op_slot(kBcOps[wall[r]][f]);
-                gwd[((size_t)f * n + k) * ng + r] = ghost ? 0.0 : hw[((size_t)slot * ng + r) * n + k];
+                gwd[((size_t)f * ng + r) * npad + k] = ghost ? 0.0 : hw[((size_t)slot * ng + r) * n + k];
             }
         }
     }
-    gh.gidx.alloc((size_t)n * ng);
-    gh.gw.alloc((size_t)4 * n * ng * ts);
+    gh.gidx.alloc((size_t)npad * ng);
+    gh.gw.alloc((size_t)4 * npad * ng * ts);
     gh.owner.alloc(ng);
     gh.tb.alloc(ng);
     gh.pos.alloc(ng);
@@ -402,25 +471,29 @@ void enqueue_ghost_fill(Problem &pb, void *U, cudaStream_t s) {
     GhostPlan &gh = pb.gh;
     const int64_t ng = gh.n_ghost;
     if (ng == 0) return;
-    const int n = pb.n;
-    int4 fc = make_int4(gh.field_class[0], gh.field_class[1], gh.field_class[2], gh.field_class[3]);
+    int fields[4] = {0, 0, 0, 0};
+    for (int f = 0; f < 4; ++f) fields[gh.field_class[f]] |= 1 << f;
+    const int4 cf = make_int4(fields[0], fields[1], fields[2], fields[3]);
+    const dim3 g1(div_up(ng * kRowLanes, 256)), g2(div_up((int64_t)gh.n_class * ng * 32, 256)), blk(256);
     if (pb.precision == 64) {
-        ghost_residual<double><<<div_up(4 * ng, 128), 128, 0, s>>>(
-            (const double *)U, pb.n_all, ng, n, gh.gidx.p, (const double *)gh.gw.p, gh.owner.p, gh.tb.p,
-            gh.pos.p, (double *)gh.res.p, pb.cp * pb.theta_bar * pb.theta_bar, pb.theta_bar, pb.g);
-        ghost_apply<double><<<div_up(4 * ng * 32, 256), 256, 0, s>>>(
-            (double *)U, pb.n_all, pb.n_prog, ng, gh.comp_of.p, gh.comp_start.p, gh.inv_off.p, gh.n_comp,
-            (const double *)gh.inv.p, (const double *)gh.res.p, gh.at.p, fc);
+        launch_kernel(ghost_residual<double>, g1, blk, s, pb.pdl, (const double *)U, pb.n_all, ng, gh.npad,
+                      (const int32_t *)gh.gidx.p, (const double *)gh.gw.p, (const int32_t *)gh.owner.p,
+                      (const unsigned char *)gh.tb.p, (const int32_t *)gh.pos.p, (double *)gh.res.p,
+                      pb.cp * pb.theta_bar * pb.theta_bar, pb.theta_bar, pb.g);
+        launch_kernel(ghost_apply<double>, g2, blk, s, pb.pdl, (double *)U, pb.n_all, pb.n_prog, ng,
+                      (const int32_t *)gh.comp_of.p, (const int64_t *)gh.comp_start.p, (const int64_t *)gh.inv_off.p,
+                      gh.n_comp, gh.n_class, (const double *)gh.inv.p, (const double *)gh.res.p,
+                      (const int32_t *)gh.at.p, cf);
     } else {
-        ghost_residual<float><<<div_up(4 * ng, 128), 128, 0, s>>>(
-            (const float *)U, pb.n_all, ng, n, gh.gidx.p, (const float *)gh.gw.p, gh.owner.p, gh.tb.p,
-            gh.pos.p, (float *)gh.res.p, (float)(pb.cp * pb.theta_bar * pb.theta_bar), (float)pb.theta_bar,
-            (float)pb.g);
-        ghost_apply<float><<<div_up(4 * ng * 32, 256), 256, 0, s>>>(
-            (float *)U, pb.n_all, pb.n_prog, ng, gh.comp_of.p, gh.comp_start.p, gh.inv_off.p, gh.n_comp,
-            (const float *)gh.inv.p, (const float *)gh.res.p, gh.at.p, fc);
+        launch_kernel(ghost_residual<float>, g1, blk, s, pb.pdl, (const float *)U, pb.n_all, ng, gh.npad,
+                      (const int32_t *)gh.gidx.p, (const float *)gh.gw.p, (const int32_t *)gh.owner.p,
+                      (const unsigned char *)gh.tb.p, (const int32_t *)gh.pos.p, (float *)gh.res.p,
+                      (float)(pb.cp * pb.theta_bar * pb.theta_bar), (float)pb.theta_bar, (float)pb.g);
+        launch_kernel(ghost_apply<float>, g2, blk, s, pb.pdl, (float *)U, pb.n_all, pb.n_prog, ng,
+                      (const int32_t *)gh.comp_of.p, (const int64_t *)gh.comp_start.p, (const int64_t *)gh.inv_off.p,
+                      gh.n_comp, gh.n_class, (const float *)gh.inv.p, (const float *)gh.res.p,
+                      (const int32_t *)gh.at.p, cf);
     }
-    RBF_CHECK_LAUNCH();
 }
 
 }  // namespace rbf

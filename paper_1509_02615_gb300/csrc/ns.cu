@@ -18,6 +18,7 @@
 // the four fields, the dissipation mu Lap + hyperviscosity on u, w, theta',
 // hyperviscosity on pi'), the tendencies of Eqs. (uEq)-(piEq), and the
 // classical RK4 update in its epilogue, so one RK4 stage is one pass.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -45,7 +46,13 @@ struct NSArgs {
     T cp, g_over_tb, theta_bar, dpibar, rd_cv;
 };
 
-template <class T, int G, bool DIFF>
+constexpr int kPrefetch = 10;   // neighbour slots per lane held in registers (prefetch variant)
+
+// One RK4 stage (or the bare right-hand side when stage < 0) for G lanes per
+// node.  PF > 0: the lane's packed weights and indices (constant data) are
+// loaded into registers before grid_dep_wait(), so they stream in while the
+// preceding ghost kernels finish; PF == 0 streams them inside the loop.
+template <class T, int G, bool DIFF, int PF>
 __global__ void __launch_bounds__(256) ns_stage_kernel(NSArgs<T> a) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int g = (int)(tid % G);
@@ -53,22 +60,48 @@ __global__ void __launch_bounds__(256) ns_stage_kernel(NSArgs<T> a) {
     const bool live = i < a.n_prog;
     if (!live) i = a.n_prog - 1;   // keep the lanes of the warp in the shuffles
     const int64_t N = a.n_all;
+    const int64_t stride = a.n_prog * G;
+    const int64_t off0 = i * G + g;
+    constexpr int R = PF > 0 ? PF : 1;
+    int jr[R];
+    T rx[R], rz[R], rd[R], rh[R];
+    if (PF > 0) {
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+            if (s < a.SL) {
+                const int64_t off = off0 + s * stride;
+                jr[s] = __ldg(a.pidx + off);
+                rx[s] = __ldg(a.wx + off);
+                rz[s] = __ldg(a.wz + off);
+                rd[s] = __ldg(a.wd + off);
+                rh[s] = __ldg(a.wh + off);
+            }
+        }
+    }
+    grid_dep_wait();     // the stage input (and its ghosts) come from earlier kernels
+    grid_dep_launch();
     const T *U = a.Uin;
     T fi0 = 0, fi1 = 0, fi2 = 0, fi3 = 0;
     if (DIFF) { fi0 = U[i]; fi1 = U[N + i]; fi2 = U[2 * N + i]; fi3 = U[3 * N + i]; }
     T ux = 0, uz = 0, ud = 0, wx_ = 0, wz_ = 0, wd_ = 0, tx = 0, tz = 0, td = 0, px = 0, pz = 0, ph = 0;
-    const int64_t stride = a.n_prog * G;
-    int64_t off = i * G + g;
-#pragma unroll 4
-    for (int s = 0; s < a.SL; ++s, off += stride) {
-        const int j = __ldg(a.pidx + off);
-        const T cx = __ldg(a.wx + off), cz = __ldg(a.wz + off), cd = __ldg(a.wd + off), ch = __ldg(a.wh + off);
+    auto accumulate = [&](int j, T cx, T cz, T cd, T ch) {
         T u = U[j], w = U[N + j], t = U[2 * N + j], p = U[3 * N + j];
         if (DIFF) { u -= fi0; w -= fi1; t -= fi2; p -= fi3; }
         ux += cx * u; uz += cz * u; ud += cd * u;
         wx_ += cx * w; wz_ += cz * w; wd_ += cd * w;
         tx += cx * t; tz += cz * t; td += cd * t;
         px += cx * p; pz += cz * p; ph += ch * p;
+    };
+    if (PF > 0) {
+#pragma unroll
+        for (int s = 0; s < R; ++s)
+            if (s < a.SL) accumulate(jr[s], rx[s], rz[s], rd[s], rh[s]);
+    } else {
+        int64_t off = off0;
+#pragma unroll 4
+        for (int s = 0; s < a.SL; ++s, off += stride)
+            accumulate(__ldg(a.pidx + off), __ldg(a.wx + off), __ldg(a.wz + off), __ldg(a.wd + off),
+                       __ldg(a.wh + off));
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
@@ -97,7 +130,8 @@ __global__ void __launch_bounds__(256) ns_stage_kernel(NSArgs<T> a) {
     if (fl & 1) k[1] = 0;   // w = 0 held on bottom/top walls
     if (fl & 2) k[0] = 0;   // u = 0 held on left/right walls
 #pragma unroll
-    for (int f = g; f < 4; f += G) {
+    for (int f = 0; f < 4; ++f) {
+        if (f % G != g) continue;   // lanes split the four fields' epilogues
         const T kf = k[f];
         if (a.stage < 0) {
             a.dUdt[f * a.n_prog + i] = kf;
@@ -137,6 +171,8 @@ __global__ void __launch_bounds__(256) adv_stage_kernel(AdvArgs<T> a) {
     int64_t i = tid / G;
     const bool live = i < a.n_prog;
     if (!live) i = a.n_prog - 1;
+    grid_dep_wait();
+    grid_dep_launch();
     T sa = 0, sh = 0;
     const int64_t stride = a.n_prog * G;
     int64_t off = i * G + g;
@@ -173,7 +209,10 @@ __global__ void __launch_bounds__(256) adv_stage_kernel(AdvArgs<T> a) {
     }
 }
 
-__global__ void advance_time(double *t, double dt) { *t += dt; }
+__global__ void advance_time(double *t, double dt) {
+    grid_dep_wait();
+    *t += dt;
+}
 
 // Packs FP64 weights [ops][n_prog][n] into [n_packed][SL][n_prog][G] of T.
 // comb[q][o]: coefficient of weight block o in packed operator q.
@@ -260,37 +299,39 @@ __global__ void minmax_kernel(const T *U, int64_t n_all, int64_t n_prog, int F, 
     }
 }
 
-template <class T, int G>
-void launch_ns_g(const NSArgs<T> &a, bool diff, cudaStream_t s) {
-    const int64_t threads = a.n_prog * G;
-    const int blocks = div_up(threads, 256);
-    if (diff) ns_stage_kernel<T, G, true><<<blocks, 256, 0, s>>>(a);
-    else ns_stage_kernel<T, G, false><<<blocks, 256, 0, s>>>(a);
+template <class T, int G, int PF>
+void launch_ns_g(const NSArgs<T> &a, cudaStream_t s, bool pdl) {
+    constexpr bool kDiff = sizeof(T) == 4;   // FP32: difference form; FP64: plain sums
+    const dim3 grid(div_up(a.n_prog * G, 256)), blk(256);
+    launch_kernel(ns_stage_kernel<T, G, kDiff, PF>, grid, blk, s, pdl, a);
 }
 
 template <class T>
-void launch_ns(const NSArgs<T> &a, int G, bool diff, cudaStream_t s) {
-    switch (G) {
-        case 1: launch_ns_g<T, 1>(a, diff, s); break;
-        case 2: launch_ns_g<T, 2>(a, diff, s); break;
-        case 4: launch_ns_g<T, 4>(a, diff, s); break;
-        case 8: launch_ns_g<T, 8>(a, diff, s); break;
+void launch_ns(const NSArgs<T> &a, int G, int pf, cudaStream_t s, bool pdl) {
+    if (pf > 0 && a.SL > kPrefetch) RBF_FAIL(RBF_E_ARG, "prefetch variant needs <= %d slots per lane", kPrefetch);
+    switch (G * 2 + (pf > 0)) {
+        case 2: launch_ns_g<T, 1, 0>(a, s, pdl); break;
+        case 3: launch_ns_g<T, 1, kPrefetch>(a, s, pdl); break;
+        case 4: launch_ns_g<T, 2, 0>(a, s, pdl); break;
+        case 5: launch_ns_g<T, 2, kPrefetch>(a, s, pdl); break;
+        case 8: launch_ns_g<T, 4, 0>(a, s, pdl); break;
+        case 9: launch_ns_g<T, 4, kPrefetch>(a, s, pdl); break;
+        case 16: launch_ns_g<T, 8, 0>(a, s, pdl); break;
+        case 17: launch_ns_g<T, 8, kPrefetch>(a, s, pdl); break;
         default: RBF_FAIL(RBF_E_ARG, "threads per node %d not in {1,2,4,8}", G);
     }
-    RBF_CHECK_LAUNCH();
 }
 
 template <class T>
-void launch_adv(const AdvArgs<T> &a, int G, cudaStream_t s) {
-    const int blocks = div_up(a.n_prog * G, 256);
+void launch_adv(const AdvArgs<T> &a, int G, cudaStream_t s, bool pdl) {
+    const dim3 grid(div_up(a.n_prog * G, 256)), blk(256);
     switch (G) {
-        case 1: adv_stage_kernel<T, 1><<<blocks, 256, 0, s>>>(a); break;
-        case 2: adv_stage_kernel<T, 2><<<blocks, 256, 0, s>>>(a); break;
-        case 4: adv_stage_kernel<T, 4><<<blocks, 256, 0, s>>>(a); break;
-        case 8: adv_stage_kernel<T, 8><<<blocks, 256, 0, s>>>(a); break;
+        case 1: launch_kernel(adv_stage_kernel<T, 1>, grid, blk, s, pdl, a); break;
+        case 2: launch_kernel(adv_stage_kernel<T, 2>, grid, blk, s, pdl, a); break;
+        case 4: launch_kernel(adv_stage_kernel<T, 4>, grid, blk, s, pdl, a); break;
+        case 8: launch_kernel(adv_stage_kernel<T, 8>, grid, blk, s, pdl, a); break;
         default: RBF_FAIL(RBF_E_ARG, "threads per node %d not in {1,2,4,8}", G);
     }
-    RBF_CHECK_LAUNCH();
 }
 
 template <class T>
@@ -350,7 +391,7 @@ void rk4_ns(Problem &pb, double dt, T *U, cudaStream_t s, bool rec, int step) {
         a.a_next = (T)(kA[st] * dt);
         a.b_stage = (T)(kB[st] * dt);
         if (rec) RBF_CUDA(cudaEventRecordWithFlags(pb.rhs_ev[(step * 4 + st) * 2], s, cudaEventRecordExternal));
-        launch_ns<T>(a, pb.G, pb.diff != 0, s);
+        launch_ns<T>(a, pb.G, pb.pf, s, pb.pdl && !rec);
         if (rec) RBF_CUDA(cudaEventRecordWithFlags(pb.rhs_ev[(step * 4 + st) * 2 + 1], s, cudaEventRecordExternal));
     }
 }
@@ -374,12 +415,11 @@ void rk4_adv(Problem &pb, double t, double dt, T *U, cudaStream_t s, bool use_td
         a.b_stage = (T)(kB[st] * dt);
         a.t_frac_dt = frac[st] * dt;
         if (rec) RBF_CUDA(cudaEventRecordWithFlags(pb.rhs_ev[(step * 4 + st) * 2], s, cudaEventRecordExternal));
-        launch_adv<T>(a, pb.G, s);
+        launch_adv<T>(a, pb.G, s, pb.pdl && !rec);
         if (rec) RBF_CUDA(cudaEventRecordWithFlags(pb.rhs_ev[(step * 4 + st) * 2 + 1], s, cudaEventRecordExternal));
     }
     if (use_tdev) {
-        advance_time<<<1, 1, 0, s>>>(pb.tdev.p, dt);
-        RBF_CHECK_LAUNCH();
+        launch_kernel(advance_time, dim3(1), dim3(1), s, pb.pdl && !rec, pb.tdev.p, dt);
     }
 }
 
@@ -456,13 +496,13 @@ void enqueue_rhs(Problem &pb, double t, void *U, void *dUdt, cudaStream_t s) {
             a.Uin = (const double *)U;
             a.dUdt = (double *)dUdt;
             a.stage = -1;
-            launch_ns<double>(a, pb.G, pb.diff != 0, s);
+            launch_ns<double>(a, pb.G, pb.pf, s, false);
         } else {
             NSArgs<float> a = ns_args<float>(pb);
             a.Uin = (const float *)U;
             a.dUdt = (float *)dUdt;
             a.stage = -1;
-            launch_ns<float>(a, pb.G, pb.diff != 0, s);
+            launch_ns<float>(a, pb.G, pb.pf, s, false);
         }
     } else {
         if (pb.precision == 64) {
@@ -471,24 +511,25 @@ void enqueue_rhs(Problem &pb, double t, void *U, void *dUdt, cudaStream_t s) {
             a.dUdt = (double *)dUdt;
             a.stage = -1;
             a.t_host = t;
-            launch_adv<double>(a, pb.G, s);
+            launch_adv<double>(a, pb.G, s, false);
         } else {
             AdvArgs<float> a = adv_args<float>(pb);
             a.Uin = (const float *)U;
             a.dUdt = (float *)dUdt;
             a.stage = -1;
             a.t_host = t;
-            launch_adv<float>(a, pb.G, s);
+            launch_adv<float>(a, pb.G, s, false);
         }
     }
 }
 
-// Autotuner: times the stage kernel for every threads-per-node choice on the
-// problem's own operators and keeps the fastest (repacking for each choice).
+// Autotuner: times the stage kernel for every (threads per node, register
+// prefetch) choice on the problem's own operators, repacking for each lane
+// count, and keeps the fastest.  NS only; advection picks G the same way.
 void autotune_threads_per_node(Problem &pb) {
     const int cands[4] = {1, 2, 4, 8};
     float best = 1e30f;
-    int bestG = 4;
+    int bestG = 4, bestPf = 0;
     cudaEvent_t e0, e1;
     RBF_CUDA(cudaEventCreate(&e0));
     RBF_CUDA(cudaEventCreate(&e1));
@@ -499,33 +540,40 @@ void autotune_threads_per_node(Problem &pb) {
     for (int G : cands) {
         pb.G = G;
         pack_operators(pb);
-        for (int rep = 0; rep < 2; ++rep) {
-            RBF_CUDA(cudaEventRecord(e0, pb.st));
-            for (int it = 0; it < 10; ++it) {
-                if (pb.kind == kNS) {
-                    if (pb.precision == 64) {
-                        NSArgs<double> a = ns_args<double>(pb);
-                        a.Uin = (const double *)U.p; a.dUdt = (double *)D.p; a.stage = -1;
-                        launch_ns<double>(a, G, pb.diff != 0, pb.st);
+        for (int pf : {0, kPrefetch}) {
+            if (pf > 0 && (pb.kind != kNS || pb.SL > kPrefetch)) continue;
+            pb.pf = pf;
+            float ms = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                RBF_CUDA(cudaEventRecord(e0, pb.st));
+                for (int it = 0; it < 10; ++it) {
+                    if (pb.kind == kNS) {
+                        if (pb.precision == 64) {
+                            NSArgs<double> a = ns_args<double>(pb);
+                            a.Uin = (const double *)U.p; a.dUdt = (double *)D.p; a.stage = -1;
+                            launch_ns<double>(a, G, pf, pb.st, false);
+                        } else {
+                            NSArgs<float> a = ns_args<float>(pb);
+                            a.Uin = (const float *)U.p; a.dUdt = (float *)D.p; a.stage = -1;
+                            launch_ns<float>(a, G, pf, pb.st, false);
+                        }
                     } else {
-                        NSArgs<float> a = ns_args<float>(pb);
-                        a.Uin = (const float *)U.p; a.dUdt = (float *)D.p; a.stage = -1;
-                        launch_ns<float>(a, G, pb.diff != 0, pb.st);
+                        enqueue_rhs(pb, 0.0, U.p, D.p, pb.st);
                     }
-                } else {
-                    enqueue_rhs(pb, 0.0, U.p, D.p, pb.st);
                 }
+                RBF_CUDA(cudaEventRecord(e1, pb.st));
+                RBF_CUDA(cudaEventSynchronize(e1));
+                float t = 0.f;
+                RBF_CUDA(cudaEventElapsedTime(&t, e0, e1));
+                ms = std::min(ms, t);
             }
-            RBF_CUDA(cudaEventRecord(e1, pb.st));
-            RBF_CUDA(cudaEventSynchronize(e1));
+            if (ms < best) { best = ms; bestG = G; bestPf = pf; }
         }
-        float ms = 0;
-        RBF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; bestG = G; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     pb.G = bestG;
+    pb.pf = bestPf;
     pack_operators(pb);
 }
 

@@ -16,9 +16,10 @@ struct GhostPlan {
     int64_t n_ghost = 0;
     int n_comp = 0;
     int n_class = 0;
+    int npad = 0;                // stencil slots per wall row, padded to 8
     int field_class[4] = {0, 0, 0, 0};
-    DevBuf<int32_t> gidx;        // [n][n_ghost] owner-stencil node per slot
-    DevBuf<unsigned char> gw;    // [F][n][n_ghost] T: BC weights, zero on ghosts
+    DevBuf<int32_t> gidx;        // [n_ghost][npad] owner-stencil node per slot
+    DevBuf<unsigned char> gw;    // [F][n_ghost][npad] T: BC weights, zero on ghosts
     DevBuf<int32_t> owner;       // [n_ghost]
     DevBuf<unsigned char> tb;    // [n_ghost] 1 if the owner is a bottom/top node
     DevBuf<int32_t> pos;         // [n_ghost] position of ghost row in component order
@@ -35,10 +36,12 @@ struct Problem {
     cudaStream_t st = nullptr;    // caller's stream
     cudaStream_t cap = nullptr;   // private stream for graph capture
     int precision = 64;
+    bool pdl = true;              // programmatic dependent launch between kernels
     int F = 4;
     int64_t n_prog = 0, n_all = 0;
     int n = 0;                    // stencil size
     int G = 4;                    // threads per node
+    int pf = 0;                   // > 0: stage kernel holds its operands in registers
     int diff = 0;                 // 1: difference form (self slot dropped)
     int n_slots = 0;              // neighbour slots per node before padding
     int SL = 0;                   // slots per lane

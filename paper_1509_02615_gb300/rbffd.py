@@ -45,7 +45,8 @@ class Info(C.Structure):
     _fields_ = [("n_prog", C.c_int64), ("n_all", C.c_int64), ("n_ghost", C.c_int64), ("n_fields", C.c_int32),
                 ("precision", C.c_int32), ("n_sten", C.c_int32), ("threads_per_node", C.c_int32),
                 ("slots", C.c_int32), ("launches_per_step", C.c_int32), ("n_components", C.c_int32),
-                ("n_ghost_classes", C.c_int32), ("weight_build_ms", C.c_double), ("ghost_setup_ms", C.c_double),
+                ("n_ghost_classes", C.c_int32), ("prefetch", C.c_int32), ("reserved", C.c_int32),
+                ("weight_build_ms", C.c_double), ("ghost_setup_ms", C.c_double),
                 ("rhs_bytes_per_node", C.c_double), ("rhs_flops_per_node", C.c_double)]
 
     def as_dict(self):

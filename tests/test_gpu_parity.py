@@ -179,6 +179,16 @@ def test_ns_fp32_rhs(dc800):
         assert rel(got[f], ref[f]) < tol, (f, rel(got[f], ref[f]))
 
 
+@pytest.mark.parametrize("G", [1, 2, 4, 8])
+def test_ns_rhs_fp32_every_lane_split(dc800, G):
+    nodes, o, U = dc800
+    pb = rbffd.ns_problem(nodes, precision=32, threads_per_node=G)
+    got = pb.rhs(0.0, rbffd.state_tensor(U, 32)).cpu().numpy().astype(np.float64)
+    ref = o.rhs(0.0, U)
+    for f, tol in zip(range(4), (2e-4, 2e-4, 2e-4, 2e-3)):
+        assert rel(got[f], ref[f]) < tol
+
+
 def test_ns_fp32_run_400m_to_300s():
     nodes = inp.density_current_nodes(400.0)
     o = NSOracle(nodes)
