@@ -73,6 +73,29 @@ int rbf_build_stencils(const double *x, const double *z, int64_t n_all, int64_t 
                        int32_t n, double period_x, int32_t *idx, void *stream);
 
 /*
+ * Allocation-free form of rbf_build_stencils (the paper has no counterpart;
+ * this is a service for callers).  Some callers may not allocate device
+ * memory: a framework whose memory pool owns the whole GPU (a cudaMalloc
+ * would bypass its accounting or fail), a process with a fixed device-memory
+ * budget, or a loop that cannot afford cudaMalloc/cudaFree's implicit device
+ * synchronisation.  This entry point calls no cudaMalloc, cudaFree or other
+ * allocating routine: its binning grid and counters live in one static
+ * device array of about 5 MB (kept by every GPU that loads the library until
+ * the process exits).  Arguments, output and ordering are those of
+ * rbf_build_stencils; the caller still provides x, z and idx.
+ *   Limits: n_all <= 262144 nodes and a binning grid of <= 262144 cells
+ *   (about n_all / 2); larger inputs return RBF_E_ARG with a message.
+ *   Set-up: the first call on each device looks up the array's device
+ *   address (cudaGetSymbolAddress) with that device current; make that first
+ *   call before any stream capture.
+ *   Sharing: every call on a device uses the same array.  Calls whose work
+ *   overlaps on the GPU (other streams or threads) race; serialise them.
+ *   Counters are cleared at the start of every call.
+ */
+int rbf_build_stencils_static(const double *x, const double *z, int64_t n_all, int64_t n_centers,
+                              int32_t n, double period_x, int32_t *idx, void *stream);
+
+/*
  * a2  RBF-FD weights (Sec. 3, Eq. (weights); Sec. 5.3, Eq. (laplacian)).
  * One augmented solve per stencil with PHS r^p (p odd, 1 <= p <= 15) and all
  * monomials of degree <= l (0 <= l <= 8), in coordinates shifted to the

@@ -10,6 +10,7 @@
 // brute-force sort over all nodes.
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -284,11 +285,142 @@ void build_stencils(const double *x, const double *z, int64_t n_all, int64_t n_c
                         : "no window holds n nodes");
 }
 
+// ---- allocation-free variant (rbf_build_stencils_static) --------------------
+// The same kernels as rbf_build_stencils, with every scratch buffer carved out
+// of one file-scope device array instead of cudaMalloc.  The array lives on
+// every GPU that loads this library until the process exits.
+namespace {
+
+constexpr int64_t kStaticMaxNodes = 262144;   // n_all limit of the static variant
+constexpr int64_t kStaticMaxCells = 262144;   // binning cells limit
+constexpr int kBboxBlocks = 64;
+
+constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+constexpr size_t kOffPart = 0;
+constexpr size_t kOffBad = kOffPart + align256(kBboxBlocks * 4 * sizeof(double));
+constexpr size_t kOffStatus = kOffBad + 256;
+constexpr size_t kOffCellOf = kOffStatus + 256;
+constexpr size_t kOffSorted = kOffCellOf + align256(kStaticMaxNodes * sizeof(int));
+constexpr size_t kOffCount = kOffSorted + align256(kStaticMaxNodes * sizeof(int));
+constexpr size_t kOffCursor = kOffCount + align256(kStaticMaxCells * sizeof(int));
+constexpr size_t kOffStart = kOffCursor + align256(kStaticMaxCells * sizeof(int));
+constexpr size_t kStaticScratchBytes = kOffStart + align256((kStaticMaxCells + 1) * sizeof(int));  // ~5 MB
+
+static __device__ __align__(256) unsigned char g_stencil_scratch[kStaticScratchBytes];
+
+std::mutex g_scratch_mu;
+unsigned char *g_scratch_addr[256] = {};
+
+// Device address of the scratch array on the current device.  In host code
+// the symbol is only a stand-in, so the address is looked up once per device
+// with that device current and cached.
+unsigned char *static_scratch() {
+    int dev = 0;
+    RBF_CUDA(cudaGetDevice(&dev));
+    RBF_REQUIRE(dev >= 0 && dev < 256, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *ptr = nullptr;
+        RBF_CUDA(cudaGetSymbolAddress(&ptr, g_stencil_scratch));
+        g_scratch_addr[dev] = static_cast<unsigned char *>(ptr);
+    }
+    return g_scratch_addr[dev];
+}
+
+}  // namespace
+
+void build_stencils_static(const double *x, const double *z, int64_t n_all, int64_t n_centers, int n,
+                           double period_x, int32_t *idx, cudaStream_t st) {
+    RBF_REQUIRE(n >= 1 && n <= 128, "stencil size n=%d must be in [1, 128]", n);
+    RBF_REQUIRE(n_all >= n, "n_all=%lld smaller than the stencil size %d", (long long)n_all, n);
+    RBF_REQUIRE(n_all <= kStaticMaxNodes, "n_all=%lld exceeds the static scratch limit of %lld nodes",
+                (long long)n_all, (long long)kStaticMaxNodes);
+    RBF_REQUIRE(n_centers >= 0 && n_centers <= n_all, "n_centers=%lld out of range", (long long)n_centers);
+    RBF_REQUIRE(period_x >= 0.0 && std::isfinite(period_x), "period_x must be finite and >= 0");
+    if (n_centers == 0) return;
+    RBF_REQUIRE(x && z && idx, "null pointer argument");
+    unsigned char *base = static_scratch();
+    double *part = reinterpret_cast<double *>(base + kOffPart);
+    int *bad = reinterpret_cast<int *>(base + kOffBad);
+    int *status = reinterpret_cast<int *>(base + kOffStatus);
+    int *cellof = reinterpret_cast<int *>(base + kOffCellOf);
+    int *sorted = reinterpret_cast<int *>(base + kOffSorted);
+    int *count = reinterpret_cast<int *>(base + kOffCount);
+    int *cursor = reinterpret_cast<int *>(base + kOffCursor);
+    int *start = reinterpret_cast<int *>(base + kOffStart);
+
+    // bounding box (the array keeps the previous call's contents: clear flags)
+    RBF_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    bbox_kernel<<<kBboxBlocks, 256, 0, st>>>(x, z, n_all, part, bad);
+    RBF_CHECK_LAUNCH();
+    double hp[kBboxBlocks * 4];
+    int hbad = 0;
+    RBF_CUDA(cudaMemcpyAsync(hp, part, sizeof(hp), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(cudaStreamSynchronize(st));
+    RBF_REQUIRE(!hbad, "non-finite node coordinates");
+    double xmin = DBL_MAX, xmax = -DBL_MAX, zmin = DBL_MAX, zmax = -DBL_MAX;
+    for (int b = 0; b < kBboxBlocks; ++b) {
+        xmin = std::fmin(xmin, hp[b * 4 + 0]); xmax = std::fmax(xmax, hp[b * 4 + 1]);
+        zmin = std::fmin(zmin, hp[b * 4 + 2]); zmax = std::fmax(zmax, hp[b * 4 + 3]);
+    }
+    // binning grid: the same rule as the allocating entry point
+    Grid g;
+    g.period = period_x;
+    double W = period_x > 0.0 ? period_x : (xmax - xmin);
+    double H = zmax - zmin;
+    double area = std::fmax(W, 1e-300) * std::fmax(H, 1e-300);
+    if (W <= 0.0 || H <= 0.0) area = std::fmax(W, H) * std::fmax(W, H) / (double)n_all;
+    double cell = std::sqrt(2.0 * area / (double)n_all);
+    if (!(cell > 0.0)) cell = 1.0;
+    g.x0 = xmin;
+    g.z0 = zmin;
+    g.ncx = (int)std::fmax(1.0, std::fmin(std::floor(W / cell), 1e6));
+    g.ncz = (int)std::fmax(1.0, std::fmin(std::ceil(H / cell), 1e6));
+    if (period_x <= 0.0 && W / g.ncx > 0) g.ncx = (int)std::fmax(1.0, std::ceil(W / cell));
+    g.cw = W > 0.0 ? W / g.ncx : cell;
+    g.ch = H > 0.0 ? H / g.ncz : cell;
+    const int64_t ncell = (int64_t)g.ncx * g.ncz;
+    RBF_REQUIRE(ncell <= kStaticMaxCells, "binning grid of %lld cells exceeds the static scratch limit of %lld",
+                (long long)ncell, (long long)kStaticMaxCells);
+
+    RBF_CUDA(cudaMemsetAsync(count, 0, ncell * sizeof(int), st));
+    RBF_CUDA(cudaMemsetAsync(cursor, 0, ncell * sizeof(int), st));
+    RBF_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+    count_kernel<<<div_up(n_all, 256), 256, 0, st>>>(x, z, n_all, g, cellof, count);
+    RBF_CHECK_LAUNCH();
+    scan_kernel<<<1, 1024, 0, st>>>(count, (int)ncell, start);
+    RBF_CHECK_LAUNCH();
+    scatter_kernel<<<div_up(n_all, 256), 256, 0, st>>>(cellof, n_all, start, cursor, sorted);
+    RBF_CHECK_LAUNCH();
+    int R0 = (int)std::ceil(std::sqrt(2.5 * n / (4.0 * 2.0)));
+    R0 = R0 < 1 ? 1 : R0;
+    const int Rmax = std::max(g.ncx, g.ncz);
+    const size_t smem = (size_t)kWarpsPerBlock * kMaxCand * (sizeof(double) + sizeof(int));
+    RBF_CUDA(cudaFuncSetAttribute(knn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    knn_kernel<<<div_up(n_centers, kWarpsPerBlock), kWarpsPerBlock * 32, smem, st>>>(
+        x, z, n_centers, n, g, start, sorted, R0, Rmax, idx, status);
+    RBF_CHECK_LAUNCH();
+    int hs = 0;
+    RBF_CUDA(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(cudaStreamSynchronize(st));
+    RBF_REQUIRE(hs == 0, "stencil search failed (%s)",
+                hs == 2 ? "more than 2048 candidates in a search window: node density too uneven"
+                        : "no window holds n nodes");
+}
+
 }  // namespace rbf
 
 extern "C" int rbf_build_stencils(const double *x, const double *z, int64_t n_all, int64_t n_centers,
                                   int32_t n, double period_x, int32_t *idx, void *stream) {
     return rbf::guarded([&] {
         rbf::build_stencils(x, z, n_all, n_centers, n, period_x, idx, rbf::as_stream(stream));
+    });
+}
+
+extern "C" int rbf_build_stencils_static(const double *x, const double *z, int64_t n_all, int64_t n_centers,
+                                         int32_t n, double period_x, int32_t *idx, void *stream) {
+    return rbf::guarded([&] {
+        rbf::build_stencils_static(x, z, n_all, n_centers, n, period_x, idx, rbf::as_stream(stream));
     });
 }

@@ -60,6 +60,7 @@ _P, _I64, _I32, _D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
 SIGNATURES = [
     ("rbf_last_error", C.c_char_p, []),
     ("rbf_build_stencils", C.c_int, [_P, _P, _I64, _I64, _I32, _D, _P, _P]),
+    ("rbf_build_stencils_static", C.c_int, [_P, _P, _I64, _I64, _I32, _D, _P, _P]),
     ("rbf_build_weights", C.c_int, [_P, _P, _I64, _P, _I64, _I32, _D, _I32, _I32, _I32, _P, _I32, _P, _P]),
     ("rbf_ns_create", C.c_int, [C.POINTER(_P), C.POINTER(NSParams), _P, _P, _I64, _I64, _P, _P, _P]),
     ("rbf_adv_create", C.c_int, [C.POINTER(_P), C.POINTER(AdvParams), _P, _P, _I64, _I64, _P, _P, _P, _P]),
