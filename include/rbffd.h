@@ -22,7 +22,9 @@
  *     buffer it passes; the library never frees them.
  *   - Node arrays list the prognostic nodes [0, n_prog) first, then ghost or
  *     reflected nodes [n_prog, n_all).
- *   - Field arrays are structure-of-arrays, field-major: U[f * n_all + i].
+ *   - Field arrays are node-major records: U[i * F + f], the F fields of node
+ *     i contiguous (F = 4: u, w, theta', pi' for Navier-Stokes; F = 1 for
+ *     advection), 16-byte aligned.
  *   - stream: a cudaStream_t (NULL = legacy default stream).  Setup calls
  *     (rbf_build_*, rbf_*_create) return after their work completes; the
  *     stepping calls (rbf_rhs, rbf_rk4_step, rbf_run) only enqueue work.
@@ -177,9 +179,9 @@ int rbf_adv_create(rbf_problem **out, const rbf_adv_params *prm, const double *x
 /*
  * a4+a5(+a6)  Right-hand side at time t.
  *   U     device, FP64 or FP32 per the problem's precision:
- *         NS [4][n_all] (ghost entries are overwritten with the solved
- *         ghost values); advection [1][n_prog]
- *   dUdt  device, same precision, [F][n_prog]
+ *         NS [n_all][4] (ghost records are overwritten with the solved
+ *         ghost values); advection [n_prog][1]
+ *   dUdt  device, same precision, [n_prog][F]
  */
 int rbf_rhs(rbf_problem *pb, double t, void *U, void *dUdt);
 
@@ -204,7 +206,7 @@ int rbf_sync(rbf_problem *pb);
 
 /*
  * Per-field minimum and maximum over the prognostic nodes of U (device,
- * layout as for rbf_rhs), written to host out_minmax [F][2].  Returns
+ * layout as for rbf_rhs), written to host out_minmax [F][2] (min, max).  Returns
  * RBF_E_NONFINITE if any prognostic value is NaN or Inf.  Synchronous.
  */
 int rbf_minmax(rbf_problem *pb, const void *U, double *out_minmax);

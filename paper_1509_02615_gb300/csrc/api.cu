@@ -87,7 +87,7 @@ void choose_threads(Problem &pb, int requested) {
                     "threads_per_node must be 0, 1, 2, 4 or 8");
         pb.G = requested;
         pack_operators(pb);
-        pb.pf = (pb.kind == kNS && pb.SL <= 10) ? 10 : 0;   // registers hold the operands when they fit
+        pb.pf = (pb.kind == kNS && pb.SLQ <= 3) ? 3 : 0;   // registers hold the operands when they fit
     }
 }
 
@@ -234,8 +234,8 @@ int rbf_ns_create(rbf_problem **out, const rbf_ns_params *prm, const double *x, 
             RBF_CUDA(cudaMemcpyAsync(pb.flags.p, fl.data(), n_prog, cudaMemcpyHostToDevice, pb.st));
 
             rbf::build_ghost_plan(pb, kind, ghost_owner);
-            rbf::choose_threads(pb, prm->threads_per_node);
             rbf::alloc_scratch(pb);
+            rbf::choose_threads(pb, prm->threads_per_node);
             RBF_CUDA(cudaStreamSynchronize(pb.st));
             *out = h;
         } catch (...) {
@@ -298,8 +298,8 @@ int rbf_adv_create(rbf_problem **out, const rbf_adv_params *prm, const double *x
             RBF_CUDA(cudaEventElapsedTime(&pb.weight_build_ms, e0, e1));
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
-            rbf::choose_threads(pb, 0);
             rbf::alloc_scratch(pb);
+            rbf::choose_threads(pb, 0);
             RBF_CUDA(cudaStreamSynchronize(pb.st));
             *out = h;
         } catch (...) {

@@ -19,6 +19,7 @@
 #include <numeric>
 
 #include "problem.cuh"
+#include "records.cuh"
 
 namespace rbf {
 
@@ -125,7 +126,8 @@ constexpr int kRowPf = 16;      // slots per lane held in registers
 constexpr int kInvPf = 16;      // inverse entries per lane held in registers
 
 // r[f][pos(r)] = b_f(r) - sum over the row's non-ghost stencil nodes, all four
-// fields at once; 8 lanes per row share the stencil slots (layout [row][slot]).
+// fields at once from one record gather per slot; 8 lanes per row share the
+// stencil slots (layout [row][slot]).  U holds node-major records [n_all][4].
 template <class T>
 __global__ void __launch_bounds__(256) ghost_residual(const T *__restrict__ U, int64_t n_all, int64_t ng, int npad,
                                                       const int32_t *__restrict__ gidx, const T *__restrict__ gw,
@@ -159,11 +161,11 @@ __global__ void __launch_bounds__(256) ghost_residual(const T *__restrict__ U, i
 #pragma unroll
     for (int t = 0; t < kRowPf; ++t) {
         if (t < per) {
-            const int j = jj[t];
-            a0 += w0[t] * U[j];
-            a1 += w1[t] * U[n_all + j];
-            a2 += w2[t] * U[2 * n_all + j];
-            a3 += w3[t] * U[3 * n_all + j];
+            const Rec<T> v = load_rec(U, jj[t]);
+            a0 += w0[t] * v.u;
+            a1 += w1[t] * v.w;
+            a2 += w2[t] * v.t;
+            a3 += w3[t] * v.p;
         }
     }
 #pragma unroll
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(256) ghost_residual(const T *__restrict__ U, i
     T b = 0;
     if (ln == 3 && tb[r]) {
         // pi'_z = g theta' / (c_p theta_bar (theta_bar + theta')) at the wall node
-        T th = U[2 * n_all + owner[r]];
+        T th = U[(int64_t)owner[r] * 4 + 2];
         b = gconst * th / (cp_tb2 + cp_tb2 / theta_bar * th);
     }
     res[ln * ng + pos[r]] = b - acc;
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(256) ghost_apply(T *__restrict__ U, int64_t n_
         if (!(fm & (1 << f))) continue;
         T s = acc[f];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) U[f * n_all + n_prog + at[q]] = s;
+        if (lane == 0) U[(n_prog + at[q]) * 4 + f] = s;
     }
 }
 

@@ -23,6 +23,7 @@
 #include <cstring>
 
 #include "problem.cuh"
+#include "records.cuh"
 
 namespace rbf {
 
@@ -30,78 +31,108 @@ namespace {
 
 template <class T>
 struct NSArgs {
-    const T *Uin;     // [4][n_all] stage input, ghosts filled
-    const T *Un;      // [4][n_all] state at the start of the step
-    T *Uout;          // [4][n_all] stage output (prognostic entries)
-    T *K;             // [4][n_prog] RK4 accumulator
-    T *dUdt;          // [4][n_prog] tendency (stage < 0)
+    const T *Uin;     // [n_all][4] stage input (node-major records), ghosts filled
+    const T *Un;      // [n_all][4] state at the start of the step
+    T *Uout;          // [n_all][4] stage output (prognostic records)
+    T *K;             // [n_prog][4] RK4 accumulator
+    T *dUdt;          // [n_prog][4] tendency (stage < 0)
     const int32_t *pidx;
     const T *wx, *wz, *wd, *wh;
     const T *pibar;
     const unsigned char *flags;
     int64_t n_prog, n_all;
-    int SL;
+    int SLQ;          // operand vectors per lane
     int stage;
     T a_next, b_stage;
     T cp, g_over_tb, theta_bar, dpibar, rd_cv;
 };
 
-constexpr int kPrefetch = 10;   // neighbour slots per lane held in registers (prefetch variant)
+// 16-byte operand vectors: 4 FP32 or 2 FP64 slots, with matching index vectors.
+template <class T>
+struct Vec;
+template <>
+struct Vec<float> {
+    static constexpr int V = 4;
+    using W = float4;
+    using I = int4;
+    __device__ static float at(const float4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+    __device__ static int at(const int4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+};
+template <>
+struct Vec<double> {
+    static constexpr int V = 2;
+    using W = double2;
+    using I = int2;
+    __device__ static double at(const double2 &v, int k) { return k == 0 ? v.x : v.y; }
+    __device__ static int at(const int2 &v, int k) { return k == 0 ? v.x : v.y; }
+};
+
+constexpr int kPrefetchVec = 3;   // operand vectors per lane held in registers (prefetch variant)
 
 // One RK4 stage (or the bare right-hand side when stage < 0) for G lanes per
-// node.  PF > 0: the lane's packed weights and indices (constant data) are
-// loaded into registers before grid_dep_wait(), so they stream in while the
-// preceding ghost kernels finish; PF == 0 streams them inside the loop.
+// node.  Each lane reads its operands as 16-byte vectors (V slots each) and
+// gathers one node record per neighbour.  PF > 0: the lane's operand vectors
+// (constant data) are loaded into registers before grid_dep_wait(), so they
+// stream in while the preceding ghost kernels finish; PF == 0 streams them.
 template <class T, int G, bool DIFF, int PF>
 __global__ void __launch_bounds__(256) ns_stage_kernel(NSArgs<T> a) {
+    using VT = Vec<T>;
+    using W = typename VT::W;
+    using I = typename VT::I;
+    constexpr int V = VT::V;
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int g = (int)(tid % G);
     int64_t i = tid / G;
     const bool live = i < a.n_prog;
     if (!live) i = a.n_prog - 1;   // keep the lanes of the warp in the shuffles
-    const int64_t N = a.n_all;
-    const int64_t stride = a.n_prog * G;
+    const int64_t stride = a.n_prog * G;   // in vectors, between consecutive q
     const int64_t off0 = i * G + g;
+    const I *pidx = reinterpret_cast<const I *>(a.pidx);
+    const W *wx = reinterpret_cast<const W *>(a.wx), *wz = reinterpret_cast<const W *>(a.wz);
+    const W *wd = reinterpret_cast<const W *>(a.wd), *wh = reinterpret_cast<const W *>(a.wh);
     constexpr int R = PF > 0 ? PF : 1;
-    int jr[R];
-    T rx[R], rz[R], rd[R], rh[R];
+    I jr[R];
+    W rx[R], rz[R], rd[R], rh[R];
     if (PF > 0) {
 #pragma unroll
-        for (int s = 0; s < R; ++s) {
-            if (s < a.SL) {
-                const int64_t off = off0 + s * stride;
-                jr[s] = __ldg(a.pidx + off);
-                rx[s] = __ldg(a.wx + off);
-                rz[s] = __ldg(a.wz + off);
-                rd[s] = __ldg(a.wd + off);
-                rh[s] = __ldg(a.wh + off);
+        for (int q = 0; q < R; ++q) {
+            if (q < a.SLQ) {
+                const int64_t off = off0 + q * stride;
+                jr[q] = __ldg(pidx + off);
+                rx[q] = __ldg(wx + off);
+                rz[q] = __ldg(wz + off);
+                rd[q] = __ldg(wd + off);
+                rh[q] = __ldg(wh + off);
             }
         }
     }
     grid_dep_wait();     // the stage input (and its ghosts) come from earlier kernels
     grid_dep_launch();
     const T *U = a.Uin;
-    T fi0 = 0, fi1 = 0, fi2 = 0, fi3 = 0;
-    if (DIFF) { fi0 = U[i]; fi1 = U[N + i]; fi2 = U[2 * N + i]; fi3 = U[3 * N + i]; }
+    Rec<T> fi = {0, 0, 0, 0};
+    if (DIFF) fi = load_rec(U, i);
     T ux = 0, uz = 0, ud = 0, wx_ = 0, wz_ = 0, wd_ = 0, tx = 0, tz = 0, td = 0, px = 0, pz = 0, ph = 0;
-    auto accumulate = [&](int j, T cx, T cz, T cd, T ch) {
-        T u = U[j], w = U[N + j], t = U[2 * N + j], p = U[3 * N + j];
-        if (DIFF) { u -= fi0; w -= fi1; t -= fi2; p -= fi3; }
-        ux += cx * u; uz += cz * u; ud += cd * u;
-        wx_ += cx * w; wz_ += cz * w; wd_ += cd * w;
-        tx += cx * t; tz += cz * t; td += cd * t;
-        px += cx * p; pz += cz * p; ph += ch * p;
+    auto vec = [&](const I &jv, const W &cx, const W &cz, const W &cd, const W &ch) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            Rec<T> r = load_rec(U, VT::at(jv, v));
+            if (DIFF) { r.u -= fi.u; r.w -= fi.w; r.t -= fi.t; r.p -= fi.p; }
+            const T x = VT::at(cx, v), z = VT::at(cz, v), d = VT::at(cd, v), h = VT::at(ch, v);
+            ux += x * r.u; uz += z * r.u; ud += d * r.u;
+            wx_ += x * r.w; wz_ += z * r.w; wd_ += d * r.w;
+            tx += x * r.t; tz += z * r.t; td += d * r.t;
+            px += x * r.p; pz += z * r.p; ph += h * r.p;
+        }
     };
     if (PF > 0) {
 #pragma unroll
-        for (int s = 0; s < R; ++s)
-            if (s < a.SL) accumulate(jr[s], rx[s], rz[s], rd[s], rh[s]);
+        for (int q = 0; q < R; ++q)
+            if (q < a.SLQ) vec(jr[q], rx[q], rz[q], rd[q], rh[q]);
     } else {
         int64_t off = off0;
-#pragma unroll 4
-        for (int s = 0; s < a.SL; ++s, off += stride)
-            accumulate(__ldg(a.pidx + off), __ldg(a.wx + off), __ldg(a.wz + off), __ldg(a.wd + off),
-                       __ldg(a.wh + off));
+#pragma unroll 2
+        for (int q = 0; q < a.SLQ; ++q, off += stride)
+            vec(__ldg(pidx + off), __ldg(wx + off), __ldg(wz + off), __ldg(wd + off), __ldg(wh + off));
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
@@ -119,33 +150,33 @@ __global__ void __launch_bounds__(256) ns_stage_kernel(NSArgs<T> a) {
         ph += __shfl_xor_sync(0xffffffffu, ph, o, G);
     }
     if (!live) return;
-    const T u = U[i], w = U[N + i], th = U[2 * N + i], pi = U[3 * N + i];
+    const Rec<T> c = DIFF ? fi : load_rec(U, i);
     const unsigned char fl = a.flags[i];
-    const T cpth = a.cp * (a.theta_bar + th);
+    const T cpth = a.cp * (a.theta_bar + c.t);
     T k[4];
-    k[0] = -u * ux - w * uz - cpth * px + ud;
-    k[1] = -u * wx_ - w * wz_ - cpth * pz + a.g_over_tb * th + wd_;
-    k[2] = -u * tx - w * tz + td;
-    k[3] = -u * px - w * (a.dpibar + pz) - a.rd_cv * (a.pibar[i] + pi) * (ux + wz_) + ph;
+    k[0] = -c.u * ux - c.w * uz - cpth * px + ud;
+    k[1] = -c.u * wx_ - c.w * wz_ - cpth * pz + a.g_over_tb * c.t + wd_;
+    k[2] = -c.u * tx - c.w * tz + td;
+    k[3] = -c.u * px - c.w * (a.dpibar + pz) - a.rd_cv * (a.pibar[i] + c.p) * (ux + wz_) + ph;
     if (fl & 1) k[1] = 0;   // w = 0 held on bottom/top walls
     if (fl & 2) k[0] = 0;   // u = 0 held on left/right walls
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         if (f % G != g) continue;   // lanes split the four fields' epilogues
         const T kf = k[f];
+        const int64_t e = i * 4 + f;
         if (a.stage < 0) {
-            a.dUdt[f * a.n_prog + i] = kf;
+            a.dUdt[e] = kf;
         } else {
-            const T un = a.Un[f * N + i];
-            T *kp = a.K + f * a.n_prog + i;
+            const T un = a.Un[e];
             if (a.stage == 0) {
-                *kp = a.b_stage * kf;
-                a.Uout[f * N + i] = un + a.a_next * kf;
+                a.K[e] = a.b_stage * kf;
+                a.Uout[e] = un + a.a_next * kf;
             } else if (a.stage < 3) {
-                *kp += a.b_stage * kf;
-                a.Uout[f * N + i] = un + a.a_next * kf;
+                a.K[e] += a.b_stage * kf;
+                a.Uout[e] = un + a.a_next * kf;
             } else {
-                a.Uout[f * N + i] = un + (*kp + a.b_stage * kf);
+                a.Uout[e] = un + (a.K[e] + a.b_stage * kf);
             }
         }
     }
@@ -214,33 +245,36 @@ __global__ void advance_time(double *t, double dt) {
     *t += dt;
 }
 
-// Packs FP64 weights [ops][n_prog][n] into [n_packed][SL][n_prog][G] of T.
+// Packs FP64 weights [ops][n_prog][n] into [n_packed][SLQ][n_prog][G][V] of T
+// (slot t = (q G + g) V + v of node i) and the indices alike.
 // comb[q][o]: coefficient of weight block o in packed operator q.
 template <class T>
 __global__ void pack_kernel(const double *__restrict__ w64, const int32_t *__restrict__ idx, int64_t n_prog,
-                            int n, int nops, int first, int n_slots, int SL, int G, int n_packed,
+                            int n, int nops, int first, int n_slots, int SLQ, int G, int V, int n_packed,
                             const double *__restrict__ comb, T *__restrict__ pw, int32_t *__restrict__ pidx) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t total = (int64_t)SL * G * n_prog;
+    const int per = SLQ * G * V;
+    int64_t total = (int64_t)per * n_prog;
     if (t >= total) return;
-    int64_t i = t / ((int64_t)SL * G);
-    int slot = (int)(t - i * SL * G);
-    int s = slot / G, g = slot - s * G;
-    int64_t dst = ((int64_t)s * n_prog + i) * G + g;
+    int64_t i = t / per;
+    int slot = (int)(t - i * per);
+    int v = slot % V, gq = slot / V;
+    int g = gq % G, q = gq / G;
+    int64_t dst = (((int64_t)q * n_prog + i) * G + g) * V + v;
     if (slot < n_slots) {
         int k = slot + first;
         pidx[dst] = idx[i * n + k];
-        for (int q = 0; q < n_packed; ++q) {
-            double v = 0.0;
+        for (int p = 0; p < n_packed; ++p) {
+            double val = 0.0;
             for (int o = 0; o < nops; ++o) {
-                double c = comb[q * nops + o];
-                if (c != 0.0) v += c * w64[((int64_t)o * n_prog + i) * n + k];
+                double c = comb[p * nops + o];
+                if (c != 0.0) val += c * w64[((int64_t)o * n_prog + i) * n + k];
             }
-            pw[(int64_t)q * total + dst] = (T)v;
+            pw[(int64_t)p * total + dst] = (T)val;
         }
     } else {
         pidx[dst] = (int32_t)i;
-        for (int q = 0; q < n_packed; ++q) pw[(int64_t)q * total + dst] = (T)0;
+        for (int p = 0; p < n_packed; ++p) pw[(int64_t)p * total + dst] = (T)0;
     }
 }
 
@@ -274,12 +308,13 @@ __global__ void pack_adv_kernel(const double *__restrict__ w64, const int32_t *_
 }
 
 template <class T>
-__global__ void minmax_kernel(const T *U, int64_t n_all, int64_t n_prog, int F, double *out, int *bad) {
-    // out[f*2+0] min, out[f*2+1] max via ordered-int atomics on doubles
+__global__ void minmax_kernel(const T *U, int64_t n_prog, int F, double *out, int *bad) {
+    // node-major records U[i * F + f]; out[f*2+0] min, out[f*2+1] max via
+    // ordered-int atomics on doubles
     for (int f = 0; f < F; ++f) {
         double lo = INFINITY, hi = -INFINITY;
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_prog; i += (int64_t)gridDim.x * blockDim.x) {
-            double v = (double)U[f * n_all + i];
+            double v = (double)U[i * F + f];
             if (!isfinite(v)) atomicExch(bad, 1);
             lo = fmin(lo, v);
             hi = fmax(hi, v);
@@ -308,16 +343,17 @@ void launch_ns_g(const NSArgs<T> &a, cudaStream_t s, bool pdl) {
 
 template <class T>
 void launch_ns(const NSArgs<T> &a, int G, int pf, cudaStream_t s, bool pdl) {
-    if (pf > 0 && a.SL > kPrefetch) RBF_FAIL(RBF_E_ARG, "prefetch variant needs <= %d slots per lane", kPrefetch);
+    if (pf > 0 && a.SLQ > kPrefetchVec)
+        RBF_FAIL(RBF_E_ARG, "prefetch variant needs <= %d operand vectors per lane", kPrefetchVec);
     switch (G * 2 + (pf > 0)) {
         case 2: launch_ns_g<T, 1, 0>(a, s, pdl); break;
-        case 3: launch_ns_g<T, 1, kPrefetch>(a, s, pdl); break;
+        case 3: launch_ns_g<T, 1, kPrefetchVec>(a, s, pdl); break;
         case 4: launch_ns_g<T, 2, 0>(a, s, pdl); break;
-        case 5: launch_ns_g<T, 2, kPrefetch>(a, s, pdl); break;
+        case 5: launch_ns_g<T, 2, kPrefetchVec>(a, s, pdl); break;
         case 8: launch_ns_g<T, 4, 0>(a, s, pdl); break;
-        case 9: launch_ns_g<T, 4, kPrefetch>(a, s, pdl); break;
+        case 9: launch_ns_g<T, 4, kPrefetchVec>(a, s, pdl); break;
         case 16: launch_ns_g<T, 8, 0>(a, s, pdl); break;
-        case 17: launch_ns_g<T, 8, kPrefetch>(a, s, pdl); break;
+        case 17: launch_ns_g<T, 8, kPrefetchVec>(a, s, pdl); break;
         default: RBF_FAIL(RBF_E_ARG, "threads per node %d not in {1,2,4,8}", G);
     }
 }
@@ -337,7 +373,7 @@ void launch_adv(const AdvArgs<T> &a, int G, cudaStream_t s, bool pdl) {
 template <class T>
 NSArgs<T> ns_args(Problem &pb) {
     NSArgs<T> a{};
-    const int64_t total = (int64_t)pb.SL * pb.G * pb.n_prog;
+    const int64_t total = (int64_t)pb.SLQ * pb.V * pb.G * pb.n_prog;
     const T *pw = (const T *)pb.pw.p;
     a.pidx = pb.pidx.p;
     a.wx = pw;
@@ -348,7 +384,7 @@ NSArgs<T> ns_args(Problem &pb) {
     a.flags = pb.flags.p;
     a.n_prog = pb.n_prog;
     a.n_all = pb.n_all;
-    a.SL = pb.SL;
+    a.SLQ = pb.SLQ;
     a.cp = (T)pb.cp;
     a.g_over_tb = (T)(pb.g / pb.theta_bar);
     a.theta_bar = (T)pb.theta_bar;
@@ -428,7 +464,10 @@ void rk4_adv(Problem &pb, double t, double dt, T *U, cudaStream_t s, bool use_td
 void pack_operators(Problem &pb) {
     const int nops = (int)pb.ops.size();
     pb.n_slots = pb.diff ? pb.n - 1 : pb.n;
-    pb.SL = div_up(pb.n_slots, pb.G);
+    // NS: 16-byte operand vectors; advection: one slot per load
+    pb.V = pb.kind == kNS ? (int)(16 / pb.tsize()) : 1;
+    pb.SLQ = div_up(pb.n_slots, pb.G * pb.V);
+    pb.SL = pb.SLQ * pb.V;
     const int64_t total = (int64_t)pb.SL * pb.G * pb.n_prog;
     pb.pidx.alloc(total);
     if (pb.kind == kAdvection) {
@@ -467,12 +506,12 @@ void pack_operators(Problem &pb) {
     pb.pw.alloc((size_t)pb.n_packed * total * pb.tsize());
     if (pb.precision == 64)
         pack_kernel<double><<<div_up(total, 256), 256, 0, pb.st>>>(pb.w64.p, pb.idx.p, pb.n_prog, pb.n, nops, pb.diff,
-                                                                   pb.n_slots, pb.SL, pb.G, pb.n_packed, dcomb.p,
-                                                                   (double *)pb.pw.p, pb.pidx.p);
+                                                                   pb.n_slots, pb.SLQ, pb.G, pb.V, pb.n_packed,
+                                                                   dcomb.p, (double *)pb.pw.p, pb.pidx.p);
     else
         pack_kernel<float><<<div_up(total, 256), 256, 0, pb.st>>>(pb.w64.p, pb.idx.p, pb.n_prog, pb.n, nops, pb.diff,
-                                                                  pb.n_slots, pb.SL, pb.G, pb.n_packed, dcomb.p,
-                                                                  (float *)pb.pw.p, pb.pidx.p);
+                                                                  pb.n_slots, pb.SLQ, pb.G, pb.V, pb.n_packed,
+                                                                  dcomb.p, (float *)pb.pw.p, pb.pidx.p);
     RBF_CHECK_LAUNCH();
     RBF_CUDA(cudaStreamSynchronize(pb.st));
 }
@@ -523,9 +562,10 @@ void enqueue_rhs(Problem &pb, double t, void *U, void *dUdt, cudaStream_t s) {
     }
 }
 
-// Autotuner: times the stage kernel for every (threads per node, register
-// prefetch) choice on the problem's own operators, repacking for each lane
-// count, and keeps the fastest.  NS only; advection picks G the same way.
+// Autotuner: for every (threads per node, register prefetch) choice it
+// repacks the operators and times whole RK4 steps through the real launch
+// path (ghost kernels, programmatic launches) on a zero state, then keeps the
+// fastest.  The advection problem times its right-hand side per lane count.
 void autotune_threads_per_node(Problem &pb) {
     const int cands[4] = {1, 2, 4, 8};
     float best = 1e30f;
@@ -534,32 +574,22 @@ void autotune_threads_per_node(Problem &pb) {
     RBF_CUDA(cudaEventCreate(&e0));
     RBF_CUDA(cudaEventCreate(&e1));
     const size_t ts = pb.tsize();
-    DevBuf<unsigned char> U((size_t)pb.F * (pb.kind == kNS ? pb.n_all : pb.n_prog) * ts);
+    const int64_t rows = pb.kind == kNS ? pb.n_all : pb.n_prog;
+    DevBuf<unsigned char> U((size_t)pb.F * rows * ts);
     DevBuf<unsigned char> D((size_t)pb.F * pb.n_prog * ts);
     RBF_CUDA(cudaMemsetAsync(U.p, 0, U.bytes(), pb.st));
     for (int G : cands) {
         pb.G = G;
         pack_operators(pb);
-        for (int pf : {0, kPrefetch}) {
-            if (pf > 0 && (pb.kind != kNS || pb.SL > kPrefetch)) continue;
+        for (int pf : {0, kPrefetchVec}) {
+            if (pf > 0 && (pb.kind != kNS || pb.SLQ > kPrefetchVec)) continue;
             pb.pf = pf;
             float ms = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {
                 RBF_CUDA(cudaEventRecord(e0, pb.st));
-                for (int it = 0; it < 10; ++it) {
-                    if (pb.kind == kNS) {
-                        if (pb.precision == 64) {
-                            NSArgs<double> a = ns_args<double>(pb);
-                            a.Uin = (const double *)U.p; a.dUdt = (double *)D.p; a.stage = -1;
-                            launch_ns<double>(a, G, pf, pb.st, false);
-                        } else {
-                            NSArgs<float> a = ns_args<float>(pb);
-                            a.Uin = (const float *)U.p; a.dUdt = (float *)D.p; a.stage = -1;
-                            launch_ns<float>(a, G, pf, pb.st, false);
-                        }
-                    } else {
-                        enqueue_rhs(pb, 0.0, U.p, D.p, pb.st);
-                    }
+                for (int it = 0; it < 4; ++it) {
+                    if (pb.kind == kNS) enqueue_rk4_step(pb, 0.0, 1e-3, U.p, pb.st, false, 0);
+                    else enqueue_rhs(pb, 0.0, U.p, D.p, pb.st);
                 }
                 RBF_CUDA(cudaEventRecord(e1, pb.st));
                 RBF_CUDA(cudaEventSynchronize(e1));
@@ -578,7 +608,6 @@ void autotune_threads_per_node(Problem &pb) {
 }
 
 void minmax(Problem &pb, const void *U, double *out) {
-    const int64_t stride = pb.kind == kNS ? pb.n_all : pb.n_prog;
     DevBuf<double> d(2 * pb.F);
     DevBuf<int> bad(1);
     std::vector<long long> init(2 * pb.F);
@@ -588,8 +617,8 @@ void minmax(Problem &pb, const void *U, double *out) {
     }
     RBF_CUDA(cudaMemcpyAsync(d.p, init.data(), d.bytes(), cudaMemcpyHostToDevice, pb.st));
     RBF_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), pb.st));
-    if (pb.precision == 64) minmax_kernel<double><<<128, 256, 0, pb.st>>>((const double *)U, stride, pb.n_prog, pb.F, d.p, bad.p);
-    else minmax_kernel<float><<<128, 256, 0, pb.st>>>((const float *)U, stride, pb.n_prog, pb.F, d.p, bad.p);
+    if (pb.precision == 64) minmax_kernel<double><<<128, 256, 0, pb.st>>>((const double *)U, pb.n_prog, pb.F, d.p, bad.p);
+    else minmax_kernel<float><<<128, 256, 0, pb.st>>>((const float *)U, pb.n_prog, pb.F, d.p, bad.p);
     RBF_CHECK_LAUNCH();
     std::vector<long long> h(2 * pb.F);
     int hb = 0;

@@ -44,7 +44,9 @@ struct Problem {
     int pf = 0;                   // > 0: stage kernel holds its operands in registers
     int diff = 0;                 // 1: difference form (self slot dropped)
     int n_slots = 0;              // neighbour slots per node before padding
-    int SL = 0;                   // slots per lane
+    int SL = 0;                   // slots per lane (padded)
+    int V = 1;                    // slots per operand vector (16 bytes for NS)
+    int SLQ = 0;                  // operand vectors per lane
     // NS physics
     double mu = 0, gamma = 0, hvc = 0, theta_bar = 300, g = 9.81, cp = 1004, cv = 717, rd = 287;
     double period_x = 0;
@@ -62,14 +64,14 @@ struct Problem {
 
     // packed operators, precision T
     int n_packed = 4;
-    DevBuf<int32_t> pidx;         // [SL][n_prog][G]
-    DevBuf<unsigned char> pw;     // T [n_packed][SL][n_prog][G]
+    DevBuf<int32_t> pidx;         // [SLQ][n_prog][G][V]
+    DevBuf<unsigned char> pw;     // T [n_packed][SLQ][n_prog][G][V]
     DevBuf<unsigned char> pibar;  // T [n_prog]
     DevBuf<unsigned char> flags;  // [n_prog]: bit0 w Dirichlet, bit1 u Dirichlet
 
     GhostPlan gh;
 
-    // RK4 scratch, precision T
+    // RK4 scratch, precision T, node-major records [rows][F]
     DevBuf<unsigned char> S0, S1, K;
     DevBuf<double> tdev;          // device time for graph replays (advection)
     DevBuf<unsigned char> host_state;  // device copy used by rbf_run_host

@@ -163,7 +163,8 @@ class Problem:
 
     @property
     def state_shape(self):
-        return (self.n_fields, self.n_all if self.kind == "ns" else self.n_prog)
+        """Node-major records: row i holds the fields of node i."""
+        return (self.n_all if self.kind == "ns" else self.n_prog, self.n_fields)
 
     def _state(self, U):
         torch = _torch()
@@ -174,7 +175,7 @@ class Problem:
     def rhs(self, t, U, dUdt=None):
         U = self._state(U)
         if dUdt is None:
-            dUdt = _torch().empty((self.n_fields, self.n_prog), dtype=self.dtype, device="cuda")
+            dUdt = _torch().empty((self.n_prog, self.n_fields), dtype=self.dtype, device="cuda")
         _check(lib().rbf_rhs(self._h, float(t), _ptr(U), _ptr(dUdt)))
         return dUdt
 
@@ -281,7 +282,16 @@ def advection_problem(nodes: inp.NodeSet, precision=64, n=37, p=7, l=4, hv_k=4, 
 
 
 def state_tensor(U, precision, device="cuda"):
-    """float64 numpy state -> contiguous tensor of the problem's precision."""
-    torch = _torch()
-    return torch.as_tensor(np.ascontiguousarray(U), dtype=torch.float64 if precision == 64 else torch.float32,
+    """Field-major float64 numpy state [F, n] -> node-major tensor [n, F] of the
+    problem's precision (the layout the library steps)."""
+    import torch
+    U = np.asarray(U, dtype=np.float64)
+    if U.ndim == 1:
+        U = U[None, :]
+    return torch.as_tensor(np.ascontiguousarray(U.T), dtype=torch.float64 if precision == 64 else torch.float32,
                            device=device).contiguous()
+
+
+def fields(t):
+    """Node-major tensor [n, F] -> field-major float64 numpy array [F, n]."""
+    return t.detach().cpu().double().numpy().T.copy()
