@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--threads-per-node", type=int, default=0, help="0 = autotuned")
+    ap.add_argument("--ens-runs", type=int, default=256, help="ensemble members (0 = skip the batched case)")
+    ap.add_argument("--ens-steps", type=int, default=40, help="timed global RK4 steps of the ensemble")
     ap.add_argument("--large-h", type=float, default=25.0,
                     help="spacing of the HBM-roofline case (0 = skip); its working set exceeds L2")
     return ap.parse_args()
@@ -200,6 +202,56 @@ def large_case(torch, args, flush):
     return out
 
 
+def ensemble_case(torch, args):
+    """Batched ensemble (FP32): 256 seeded density-current members of uneven
+    size (spacings 50-400 m, Cartesian/hexagonal/scattered, stencils 31-75),
+    stepped together; the timed region is the first ens_steps global RK4
+    steps (every member active), inputs ~8 GB (larger than L2)."""
+    from paper_1509_02615_gb300 import inputs as inp
+    from paper_1509_02615_gb300 import rbffd
+    pk, pk_kind = peaks()
+    t0 = time.perf_counter()
+    members = inp.ensemble_members(args.ens_runs, seed=0)
+    t_gen = time.perf_counter() - t0
+    ens = rbffd.ensemble_problem(members, precision=32)
+    info = ens.info()
+    U = ens.state()
+    stream = torch.cuda.current_stream()
+    ens.run(3, U)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    K = args.ens_steps
+    e0.record(stream)
+    ens.run(K, U)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    upd = ens.node_updates(K)
+    ens.set_stage_timing(True)
+    stage = []
+    for _ in range(3):
+        ens.run(1, U)
+        stage.append(ens.stage_kernel_ms() / 4.0)
+    ens.set_stage_timing(False)
+    mm = ens.minmax(U)
+    avg = float(np.median(stage))
+    bpl = info["rhs_bytes_per_node"] * ens.n_prog
+    ach = bpl / (avg / 1e3) / 1e9
+    out = {"workload": f"{len(members)} density-current members, {ens.n_prog} nodes + {ens.n_all - ens.n_prog} ghosts, "
+                       f"h in 50-400 m, cart/hex/scattered, n 31-75, FP32",
+           "value": upd / (ms / 1e3), "unit": "node-updates/s", "node_rhs_per_s": 4.0 * upd / (ms / 1e3),
+           "timed_global_steps": K, "ms": ms, "node_updates_to_900s": ens.node_updates(-1),
+           "threads_per_node": info["threads_per_node"],
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": ach / pk["hbm_gbs"], "traffic": None, "kernel": "ens_stage_kernel",
+                        "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg,
+                        "peak_source": f"{pk_kind} hbm_gbs"},
+           "setup": {"host_node_generation_s": t_gen, "gpu_build_ms": info["weight_build_ms"]},
+           "finite": bool(np.all(np.isfinite(mm)))}
+    ens.close()
+    return out
+
+
 def cpu_baseline(h, budget_s=12.0):
     """FP64 oracle on a 1/8-width periodic strip of the same workload (same
     spacing, stencils, operators and boundary treatment): node-RHS/s."""
@@ -328,6 +380,9 @@ def main():
     large = None
     if args.large_h > 0:
         large = large_case(torch, args, flush)
+    batched = None
+    if args.ens_runs > 0:
+        batched = ensemble_case(torch, args)
 
     base = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -346,7 +401,7 @@ def main():
                 "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
                 "gpu_launches": info["launches_per_step"] * args.steps,
                 "setup": {"weight_build_ms": info["weight_build_ms"], "ghost_setup_ms": info["ghost_setup_ms"]},
-                "fp64": fp64, "roofline_large": large, "cpu_baseline": base,
+                "fp64": fp64, "roofline_large": large, "batched": batched, "cpu_baseline": base,
                 "state_minmax": {"theta_min": mm[2, 0], "w_min": mm[1, 0], "w_max": mm[1, 1]}}
         print(json.dumps(line), flush=True)
     pb.close()

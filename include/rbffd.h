@@ -176,6 +176,43 @@ int rbf_adv_create(rbf_problem **out, const rbf_adv_params *prm, const double *x
                    int64_t n_prog, int64_t n_all, const int32_t *src, const double *U,
                    const double *V, void *stream);
 
+/* One member of a batched ensemble (a8). */
+typedef struct rbf_ens_member {
+    int64_t n_prog, n_all;  /* member's prognostic nodes and all nodes (ghosts last) */
+    int32_t n_sten;         /* its stencil size                                   */
+    int32_t poly_l;         /* its polynomial degree                              */
+    double period_x;        /* > 0: periodic in x                                 */
+    double gamma;           /* its hyperviscosity coefficient                     */
+    double dt;              /* its RK4 time step                                  */
+    int64_t n_steps;        /* steps to its end time                              */
+} rbf_ens_member;
+
+/*
+ * a8  Batched ensemble of Navier-Stokes runs of uneven size (no counterpart
+ * in the paper, which runs one case at a time; each member is the method of
+ * Secs. 3, 5.2, 5.3 and 6.2-6.3 with its own nodes, stencil size, degree,
+ * spacing and dt).  common supplies the physics, PHS exponents, hyperviscosity
+ * power and precision; its n_sten, poly_l, period_x and gamma are replaced
+ * per member.  x, z are the members' node arrays concatenated (host, double);
+ * kind concatenates the members' prognostic kinds and ghost_owner their ghost
+ * owners (member-local indices), as for rbf_ns_create.  The state is the
+ * members' node-major records concatenated in the same order
+ * ([sum n_all][4]).  Threads per node are autotuned for the whole ensemble.
+ */
+int rbf_ens_create(rbf_problem **out, const rbf_ns_params *common, int32_t n_members,
+                   const rbf_ens_member *members, const double *x, const double *z, const int32_t *kind,
+                   const int32_t *ghost_owner, void *stream);
+
+/*
+ * Advances every member by min(max_steps, its n_steps) RK4 steps of its own
+ * dt (max_steps < 0: to each member's end); members that finish drop out of
+ * the launches.  Asynchronous on the problem's stream.
+ */
+int rbf_ens_run(rbf_problem *pb, int64_t max_steps, void *U);
+
+/* Node updates (prognostic nodes x steps) that rbf_ens_run(max_steps) performs. */
+int rbf_ens_node_updates(const rbf_problem *pb, int64_t max_steps, double *out);
+
 /*
  * a4+a5(+a6)  Right-hand side at time t.
  *   U     device, FP64 or FP32 per the problem's precision:

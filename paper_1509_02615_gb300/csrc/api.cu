@@ -67,6 +67,8 @@ void common_setup(Problem &pb, const double *x, const double *z, int64_t n_prog,
     pb.tdev.alloc(1);
 }
 
+}  // namespace
+
 void alloc_scratch(Problem &pb) {
     const int64_t stride = pb.kind == kNS ? pb.n_all : pb.n_prog;
     const size_t ts = pb.tsize();
@@ -78,6 +80,8 @@ void alloc_scratch(Problem &pb) {
     RBF_CUDA(cudaMemsetAsync(pb.S0.p, 0, pb.S0.bytes(), pb.st));
     RBF_CUDA(cudaMemsetAsync(pb.S1.p, 0, pb.S1.bytes(), pb.st));
 }
+
+namespace {
 
 void choose_threads(Problem &pb, int requested) {
     if (requested == 0) {
@@ -151,6 +155,85 @@ void run(Problem &pb, double t0, double dt, int64_t n_steps, void *U) {
 }
 
 }  // namespace
+
+// Builds a Navier-Stokes problem (stencils, weights, packing, ghost systems).
+// with_scratch = false leaves out the RK4 stage buffers (ensemble members
+// step in their ensemble's buffers).
+void build_ns(Problem &pb, const rbf_ns_params &prm, const double *x, const double *z, int64_t n_prog,
+          int64_t n_all, const int32_t *kind, const int32_t *ghost_owner, void *stream, bool with_scratch) {
+    RBF_REQUIRE(prm.precision == 64 || prm.precision == 32, "precision must be 64 or 32");
+    RBF_REQUIRE(prm.n_sten >= 2, "stencil size must be >= 2");
+    RBF_REQUIRE(prm.mu >= 0.0 && prm.gamma >= 0.0, "mu and gamma must be >= 0");
+    RBF_REQUIRE(prm.theta_bar > 0.0 && prm.cp > 0.0 && prm.cv > 0.0, "bad physical constants");
+    RBF_REQUIRE(kind != nullptr, "null kind");
+    RBF_REQUIRE(n_all == n_prog || ghost_owner != nullptr, "ghosts need ghost_owner");
+    RBF_REQUIRE(with_scratch || prm.threads_per_node != 0, "autotuning needs the stage buffers");
+    pb.kind = rbf::kNS;
+    pb.F = 4;
+    rbf::common_setup(pb, x, z, n_prog, n_all, stream);
+    pb.precision = prm.precision;
+    pb.n = prm.n_sten;
+    pb.p = prm.phs_p;
+    pb.l = prm.poly_l;
+    pb.hv_k = prm.hv_k;
+    pb.hv_p = prm.hv_p;
+    pb.period_x = prm.period_x;
+    pb.mu = prm.mu;
+    pb.gamma = prm.gamma;
+    pb.hvc = prm.hv_k > 0 ? ((prm.hv_k % 2 == 1) ? 1.0 : -1.0) * prm.gamma : 0.0;  // (-1)^(k+1) gamma
+    pb.theta_bar = prm.theta_bar;
+    pb.g = prm.g;
+    pb.cp = prm.cp;
+    pb.cv = prm.cv;
+    pb.rd = prm.rd;
+    pb.diff = pb.precision == 32 ? 1 : 0;
+    for (int64_t i = 0; i < n_prog; ++i)
+        RBF_REQUIRE(kind[i] >= 0 && kind[i] <= 4, "kind[%lld]=%d not in [0, 4]", (long long)i, kind[i]);
+
+    cudaEvent_t e0, e1;
+    RBF_CUDA(cudaEventCreate(&e0));
+    RBF_CUDA(cudaEventCreate(&e1));
+    RBF_CUDA(cudaEventRecord(e0, pb.st));
+    pb.idx.alloc((size_t)n_prog * pb.n);
+    rbf::build_stencils(pb.x.p, pb.z.p, n_all, n_prog, pb.n, pb.period_x, pb.idx.p, pb.st);
+    pb.ops = {RBF_OP_DX, RBF_OP_DZ, RBF_OP_LAP, RBF_OP_DXX, RBF_OP_DZZ};
+    const int nbase = (int)pb.ops.size();
+    if (pb.hv_k > 0) pb.ops.push_back(RBF_OP_HV);
+    pb.w64.alloc(pb.ops.size() * (size_t)n_prog * pb.n);
+    rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, pb.period_x, pb.p, pb.l, 0, pb.ops.data(),
+                       nbase, pb.w64.p, pb.st);
+    if (pb.hv_k > 0) {
+        int hv = RBF_OP_HV;
+        rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, pb.period_x, pb.hv_p, pb.l, pb.hv_k, &hv,
+                           1, pb.w64.p + (size_t)nbase * n_prog * pb.n, pb.st);
+    }
+    RBF_CUDA(cudaEventRecord(e1, pb.st));
+    RBF_CUDA(cudaEventSynchronize(e1));
+    RBF_CUDA(cudaEventElapsedTime(&pb.weight_build_ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+
+    // per-node background Exner pressure and Dirichlet flags
+    pb.pibar.alloc((size_t)n_prog * pb.tsize());
+    if (pb.precision == 64)
+        rbf::pibar_kernel<double><<<rbf::div_up(n_prog, 256), 256, 0, pb.st>>>(pb.z.p, n_prog, pb.g, pb.cp,
+                                                                             pb.theta_bar, (double *)pb.pibar.p);
+    else
+        rbf::pibar_kernel<float><<<rbf::div_up(n_prog, 256), 256, 0, pb.st>>>(pb.z.p, n_prog, pb.g, pb.cp,
+                                                                            pb.theta_bar, (float *)pb.pibar.p);
+    RBF_CHECK_LAUNCH();
+    std::vector<unsigned char> fl(n_prog);
+    for (int64_t i = 0; i < n_prog; ++i)
+        fl[i] = (kind[i] == 1 || kind[i] == 2) ? 1 : (kind[i] == 3 || kind[i] == 4) ? 2 : 0;
+    pb.flags.alloc(n_prog);
+    RBF_CUDA(cudaMemcpyAsync(pb.flags.p, fl.data(), n_prog, cudaMemcpyHostToDevice, pb.st));
+
+    rbf::build_ghost_plan(pb, kind, ghost_owner);
+    if (with_scratch) rbf::alloc_scratch(pb);
+    rbf::choose_threads(pb, prm.threads_per_node);
+    RBF_CUDA(cudaStreamSynchronize(pb.st));
+}
+
 }  // namespace rbf
 
 using rbf::Problem;
@@ -164,79 +247,9 @@ int rbf_ns_create(rbf_problem **out, const rbf_ns_params *prm, const double *x, 
     return rbf::guarded([&] {
         RBF_REQUIRE(out && prm, "null argument");
         *out = nullptr;
-        RBF_REQUIRE(prm->precision == 64 || prm->precision == 32, "precision must be 64 or 32");
-        RBF_REQUIRE(prm->n_sten >= 2, "stencil size must be >= 2");
-        RBF_REQUIRE(prm->mu >= 0.0 && prm->gamma >= 0.0, "mu and gamma must be >= 0");
-        RBF_REQUIRE(prm->theta_bar > 0.0 && prm->cp > 0.0 && prm->cv > 0.0, "bad physical constants");
-        RBF_REQUIRE(kind != nullptr, "null kind");
-        RBF_REQUIRE(n_all == n_prog || ghost_owner != nullptr, "ghosts need ghost_owner");
         auto *h = new rbf_problem();
         try {
-            Problem &pb = h->impl;
-            pb.kind = rbf::kNS;
-            pb.F = 4;
-            rbf::common_setup(pb, x, z, n_prog, n_all, stream);
-            pb.precision = prm->precision;
-            pb.n = prm->n_sten;
-            pb.p = prm->phs_p;
-            pb.l = prm->poly_l;
-            pb.hv_k = prm->hv_k;
-            pb.hv_p = prm->hv_p;
-            pb.period_x = prm->period_x;
-            pb.mu = prm->mu;
-            pb.gamma = prm->gamma;
-            pb.hvc = prm->hv_k > 0 ? ((prm->hv_k % 2 == 1) ? 1.0 : -1.0) * prm->gamma : 0.0;  // (-1)^(k+1) gamma
-            pb.theta_bar = prm->theta_bar;
-            pb.g = prm->g;
-            pb.cp = prm->cp;
-            pb.cv = prm->cv;
-            pb.rd = prm->rd;
-            pb.diff = pb.precision == 32 ? 1 : 0;
-            for (int64_t i = 0; i < n_prog; ++i)
-                RBF_REQUIRE(kind[i] >= 0 && kind[i] <= 4, "kind[%lld]=%d not in [0, 4]", (long long)i, kind[i]);
-
-            cudaEvent_t e0, e1;
-            RBF_CUDA(cudaEventCreate(&e0));
-            RBF_CUDA(cudaEventCreate(&e1));
-            RBF_CUDA(cudaEventRecord(e0, pb.st));
-            pb.idx.alloc((size_t)n_prog * pb.n);
-            rbf::build_stencils(pb.x.p, pb.z.p, n_all, n_prog, pb.n, pb.period_x, pb.idx.p, pb.st);
-            pb.ops = {RBF_OP_DX, RBF_OP_DZ, RBF_OP_LAP, RBF_OP_DXX, RBF_OP_DZZ};
-            const int nbase = (int)pb.ops.size();
-            if (pb.hv_k > 0) pb.ops.push_back(RBF_OP_HV);
-            pb.w64.alloc(pb.ops.size() * (size_t)n_prog * pb.n);
-            rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, pb.period_x, pb.p, pb.l, 0, pb.ops.data(),
-                               nbase, pb.w64.p, pb.st);
-            if (pb.hv_k > 0) {
-                int hv = RBF_OP_HV;
-                rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, pb.period_x, pb.hv_p, pb.l, pb.hv_k, &hv,
-                                   1, pb.w64.p + (size_t)nbase * n_prog * pb.n, pb.st);
-            }
-            RBF_CUDA(cudaEventRecord(e1, pb.st));
-            RBF_CUDA(cudaEventSynchronize(e1));
-            RBF_CUDA(cudaEventElapsedTime(&pb.weight_build_ms, e0, e1));
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-
-            // per-node background Exner pressure and Dirichlet flags
-            pb.pibar.alloc((size_t)n_prog * pb.tsize());
-            if (pb.precision == 64)
-                rbf::pibar_kernel<double><<<rbf::div_up(n_prog, 256), 256, 0, pb.st>>>(pb.z.p, n_prog, pb.g, pb.cp,
-                                                                                     pb.theta_bar, (double *)pb.pibar.p);
-            else
-                rbf::pibar_kernel<float><<<rbf::div_up(n_prog, 256), 256, 0, pb.st>>>(pb.z.p, n_prog, pb.g, pb.cp,
-                                                                                    pb.theta_bar, (float *)pb.pibar.p);
-            RBF_CHECK_LAUNCH();
-            std::vector<unsigned char> fl(n_prog);
-            for (int64_t i = 0; i < n_prog; ++i)
-                fl[i] = (kind[i] == 1 || kind[i] == 2) ? 1 : (kind[i] == 3 || kind[i] == 4) ? 2 : 0;
-            pb.flags.alloc(n_prog);
-            RBF_CUDA(cudaMemcpyAsync(pb.flags.p, fl.data(), n_prog, cudaMemcpyHostToDevice, pb.st));
-
-            rbf::build_ghost_plan(pb, kind, ghost_owner);
-            rbf::alloc_scratch(pb);
-            rbf::choose_threads(pb, prm->threads_per_node);
-            RBF_CUDA(cudaStreamSynchronize(pb.st));
+            rbf::build_ns(h->impl, *prm, x, z, n_prog, n_all, kind, ghost_owner, stream, true);
             *out = h;
         } catch (...) {
             delete h;
@@ -312,6 +325,7 @@ int rbf_adv_create(rbf_problem **out, const rbf_adv_params *prm, const double *x
 int rbf_rhs(rbf_problem *h, double t, void *U, void *dUdt) {
     return rbf::guarded([&] {
         RBF_REQUIRE(h && U && dUdt, "null argument");
+        RBF_REQUIRE(h->impl.kind != rbf::kEnsemble, "ensembles step with rbf_ens_run");
         rbf::enqueue_rhs(h->impl, t, U, dUdt, h->impl.st);
     });
 }
@@ -320,6 +334,7 @@ int rbf_rk4_step(rbf_problem *h, double t, double dt, void *U) {
     return rbf::guarded([&] {
         RBF_REQUIRE(h && U, "null argument");
         RBF_REQUIRE(std::isfinite(dt) && std::isfinite(t), "non-finite time or step");
+        RBF_REQUIRE(h->impl.kind != rbf::kEnsemble, "ensembles step with rbf_ens_run");
         rbf::enqueue_rk4_step(h->impl, t, dt, U, h->impl.st, false, 0);
     });
 }
@@ -327,6 +342,7 @@ int rbf_rk4_step(rbf_problem *h, double t, double dt, void *U) {
 int rbf_run(rbf_problem *h, double t0, double dt, int64_t n_steps, void *U) {
     return rbf::guarded([&] {
         RBF_REQUIRE(h, "null problem");
+        RBF_REQUIRE(h->impl.kind != rbf::kEnsemble, "ensembles step with rbf_ens_run");
         rbf::run(h->impl, t0, dt, n_steps, U);
     });
 }
@@ -374,7 +390,7 @@ int rbf_get_info(const rbf_problem *h, rbf_info *out) {
         out->n_sten = pb.n;
         out->threads_per_node = pb.G;
         out->slots = pb.SL * pb.G;
-        const bool ghosts = pb.kind == rbf::kNS && pb.gh.n_ghost > 0;
+        const bool ghosts = pb.kind != rbf::kAdvection && pb.gh.n_ghost > 0;
         out->launches_per_step = 4 * (ghosts ? 3 : 1) + (pb.kind == rbf::kAdvection ? 1 : 0);
         out->n_components = pb.gh.n_comp;
         out->n_ghost_classes = pb.gh.n_class;
@@ -382,8 +398,13 @@ int rbf_get_info(const rbf_problem *h, rbf_info *out) {
         out->weight_build_ms = pb.weight_build_ms;
         out->ghost_setup_ms = pb.ghost_setup_ms;
         const double ts = (double)pb.tsize();
-        const double slots = pb.n_slots;   // algorithmic, without padding
-        if (pb.kind == rbf::kNS) {
+        double slots = pb.n_slots;   // algorithmic, without padding
+        if (pb.kind == rbf::kEnsemble) {   // node-weighted mean over the members
+            double s = 0.0;
+            for (auto &m : pb.ens->members) s += (double)m->n_slots * (double)m->n_prog;
+            slots = s / (double)pb.n_prog;
+        }
+        if (pb.kind != rbf::kAdvection) {
             // packed weights (4 operators) + index per slot, the node's own
             // values, U_n, the RK4 accumulator read+write, the stage output,
             // pibar and the flag byte

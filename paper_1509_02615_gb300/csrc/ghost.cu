@@ -129,7 +129,7 @@ constexpr int kInvPf = 16;      // inverse entries per lane held in registers
 // fields at once from one record gather per slot; 8 lanes per row share the
 // stencil slots (layout [row][slot]).  U holds node-major records [n_all][4].
 template <class T>
-__global__ void __launch_bounds__(256) ghost_residual(const T *__restrict__ U, int64_t n_all, int64_t ng, int npad,
+__global__ void __launch_bounds__(256) ghost_residual(const T *__restrict__ U, int64_t ng, int64_t rows, int npad,
                                                       const int32_t *__restrict__ gidx, const T *__restrict__ gw,
                                                       const int32_t *__restrict__ owner,
                                                       const unsigned char *__restrict__ tb,
@@ -138,8 +138,8 @@ __global__ void __launch_bounds__(256) ghost_residual(const T *__restrict__ U, i
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t r = tid / kRowLanes;
     const int ln = (int)(tid % kRowLanes);
-    const bool live = r < ng;
-    if (!live) r = ng - 1;
+    const bool live = r < rows;
+    if (!live) r = rows - 1;
     const int per = npad / kRowLanes;
     // constant operands first: they do not depend on the previous kernel
     int jj[kRowPf];
@@ -188,20 +188,21 @@ __global__ void __launch_bounds__(256) ghost_residual(const T *__restrict__ U, i
 
 // u_G = W_G^{-1} r within each component: one warp per (class, position)
 // computes every field of that boundary-operator class from one pass over
-// the inverse row (held in registers before the wait).
+// the inverse row (held in registers before the wait).  grec[q] is the state
+// record of the ghost at position q; rows <= ng positions are processed.
 template <class T>
-__global__ void __launch_bounds__(256) ghost_apply(T *__restrict__ U, int64_t n_all, int64_t n_prog, int64_t ng,
+__global__ void __launch_bounds__(256) ghost_apply(T *__restrict__ U, int64_t ng, int64_t rows,
                                                    const int32_t *__restrict__ comp_of,
                                                    const int64_t *__restrict__ comp_start,
                                                    const int64_t *__restrict__ inv_off, int n_comp, int n_class,
                                                    const T *__restrict__ inv, const T *__restrict__ res,
-                                                   const int32_t *__restrict__ at, int4 cls_fields) {
+                                                   const int64_t *__restrict__ grec, int4 cls_fields) {
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    const bool live = wid < (int64_t)n_class * ng;
+    const bool live = wid < (int64_t)n_class * rows;
     const int64_t w = live ? wid : 0;
-    const int cls = (int)(w / ng);
-    const int64_t q = w - (int64_t)cls * ng;
+    const int cls = (int)(w / rows);
+    const int64_t q = w - (int64_t)cls * rows;
     const int c = comp_of[q];
     const int64_t s0 = comp_start[c];
     const int m = (int)(comp_start[c + 1] - s0);
@@ -231,7 +232,7 @@ __global__ void __launch_bounds__(256) ghost_apply(T *__restrict__ U, int64_t n_
         if (!(fm & (1 << f))) continue;
         T s = acc[f];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) U[(n_prog + at[q]) * 4 + f] = s;
+        if (lane == 0) U[grec[q] * 4 + f] = s;
     }
 }
 
@@ -348,6 +349,7 @@ void build_ghost_plan(Problem &pb, const int32_t *kind_host, const int32_t *owne
     const int ncl = (int)patterns.size();
     gh.n_comp = nc;
     gh.n_class = ncl;
+    gh.rows = ng;
 
     // dense W_G blocks, one per (class, component)
     std::vector<int> msize;
@@ -442,7 +444,7 @@ void build_ghost_plan(Problem &pb, const int32_t *kind_host, const int32_t *owne
     gh.owner.alloc(ng);
     gh.tb.alloc(ng);
     gh.pos.alloc(ng);
-    gh.at.alloc(ng);
+    gh.grec.alloc(ng);
     gh.comp_of.alloc(ng);
     gh.comp_start.alloc(nc + 1);
     gh.inv_off.alloc(nm);
@@ -458,7 +460,10 @@ void build_ghost_plan(Problem &pb, const int32_t *kind_host, const int32_t *owne
     RBF_CUDA(cudaMemcpyAsync(gh.owner.p, owner_host, ng * 4, cudaMemcpyHostToDevice, st));
     RBF_CUDA(cudaMemcpyAsync(gh.tb.p, tbv.data(), ng, cudaMemcpyHostToDevice, st));
     RBF_CUDA(cudaMemcpyAsync(gh.pos.p, pos.data(), ng * 4, cudaMemcpyHostToDevice, st));
-    RBF_CUDA(cudaMemcpyAsync(gh.at.p, at.data(), ng * 4, cudaMemcpyHostToDevice, st));
+    std::vector<int64_t> grec(ng);
+    for (int64_t q = 0; q < ng; ++q) grec[q] = pb.n_prog + at[q];
+    RBF_CUDA(cudaMemcpyAsync(gh.grec.p, grec.data(), ng * 8, cudaMemcpyHostToDevice, st));
+    RBF_CUDA(cudaStreamSynchronize(st));
     RBF_CUDA(cudaMemcpyAsync(gh.comp_of.p, comp_of.data(), ng * 4, cudaMemcpyHostToDevice, st));
     RBF_CUDA(cudaMemcpyAsync(gh.comp_start.p, cstart.data(), (nc + 1) * 8, cudaMemcpyHostToDevice, st));
     RBF_CUDA(cudaMemcpyAsync(gh.inv_off.p, moff.data(), nm * 8, cudaMemcpyHostToDevice, st));
@@ -471,30 +476,30 @@ void build_ghost_plan(Problem &pb, const int32_t *kind_host, const int32_t *owne
 
 void enqueue_ghost_fill(Problem &pb, void *U, cudaStream_t s) {
     GhostPlan &gh = pb.gh;
-    const int64_t ng = gh.n_ghost;
-    if (ng == 0) return;
+    const int64_t ng = gh.n_ghost, rows = gh.rows;
+    if (ng == 0 || rows == 0) return;
     int fields[4] = {0, 0, 0, 0};
     for (int f = 0; f < 4; ++f) fields[gh.field_class[f]] |= 1 << f;
     const int4 cf = make_int4(fields[0], fields[1], fields[2], fields[3]);
-    const dim3 g1(div_up(ng * kRowLanes, 256)), g2(div_up((int64_t)gh.n_class * ng * 32, 256)), blk(256);
+    const dim3 g1(div_up(rows * kRowLanes, 256)), g2(div_up((int64_t)gh.n_class * rows * 32, 256)), blk(256);
     if (pb.precision == 64) {
-        launch_kernel(ghost_residual<double>, g1, blk, s, pb.pdl, (const double *)U, pb.n_all, ng, gh.npad,
+        launch_kernel(ghost_residual<double>, g1, blk, s, pb.pdl, (const double *)U, ng, rows, gh.npad,
                       (const int32_t *)gh.gidx.p, (const double *)gh.gw.p, (const int32_t *)gh.owner.p,
                       (const unsigned char *)gh.tb.p, (const int32_t *)gh.pos.p, (double *)gh.res.p,
                       pb.cp * pb.theta_bar * pb.theta_bar, pb.theta_bar, pb.g);
-        launch_kernel(ghost_apply<double>, g2, blk, s, pb.pdl, (double *)U, pb.n_all, pb.n_prog, ng,
+        launch_kernel(ghost_apply<double>, g2, blk, s, pb.pdl, (double *)U, ng, rows,
                       (const int32_t *)gh.comp_of.p, (const int64_t *)gh.comp_start.p, (const int64_t *)gh.inv_off.p,
                       gh.n_comp, gh.n_class, (const double *)gh.inv.p, (const double *)gh.res.p,
-                      (const int32_t *)gh.at.p, cf);
+                      (const int64_t *)gh.grec.p, cf);
     } else {
-        launch_kernel(ghost_residual<float>, g1, blk, s, pb.pdl, (const float *)U, pb.n_all, ng, gh.npad,
+        launch_kernel(ghost_residual<float>, g1, blk, s, pb.pdl, (const float *)U, ng, rows, gh.npad,
                       (const int32_t *)gh.gidx.p, (const float *)gh.gw.p, (const int32_t *)gh.owner.p,
                       (const unsigned char *)gh.tb.p, (const int32_t *)gh.pos.p, (float *)gh.res.p,
                       (float)(pb.cp * pb.theta_bar * pb.theta_bar), (float)pb.theta_bar, (float)pb.g);
-        launch_kernel(ghost_apply<float>, g2, blk, s, pb.pdl, (float *)U, pb.n_all, pb.n_prog, ng,
+        launch_kernel(ghost_apply<float>, g2, blk, s, pb.pdl, (float *)U, ng, rows,
                       (const int32_t *)gh.comp_of.p, (const int64_t *)gh.comp_start.p, (const int64_t *)gh.inv_off.p,
                       gh.n_comp, gh.n_class, (const float *)gh.inv.p, (const float *)gh.res.p,
-                      (const int32_t *)gh.at.p, cf);
+                      (const int64_t *)gh.grec.p, cf);
     }
 }
 

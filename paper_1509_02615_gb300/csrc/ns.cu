@@ -617,8 +617,10 @@ void minmax(Problem &pb, const void *U, double *out) {
     }
     RBF_CUDA(cudaMemcpyAsync(d.p, init.data(), d.bytes(), cudaMemcpyHostToDevice, pb.st));
     RBF_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), pb.st));
-    if (pb.precision == 64) minmax_kernel<double><<<128, 256, 0, pb.st>>>((const double *)U, pb.n_prog, pb.F, d.p, bad.p);
-    else minmax_kernel<float><<<128, 256, 0, pb.st>>>((const float *)U, pb.n_prog, pb.F, d.p, bad.p);
+    // an ensemble's records interleave members' ghosts: scan every record
+    const int64_t rows = pb.kind == kEnsemble ? pb.n_all : pb.n_prog;
+    if (pb.precision == 64) minmax_kernel<double><<<128, 256, 0, pb.st>>>((const double *)U, rows, pb.F, d.p, bad.p);
+    else minmax_kernel<float><<<128, 256, 0, pb.st>>>((const float *)U, rows, pb.F, d.p, bad.p);
     RBF_CHECK_LAUNCH();
     std::vector<long long> h(2 * pb.F);
     int hb = 0;

@@ -4,26 +4,44 @@
 
 #include <cuda_runtime.h>
 
+#include <memory>
 #include <vector>
 
 #include "common.cuh"
 
 namespace rbf {
 
-enum ProblemKind { kNS = 0, kAdvection = 1 };
+enum ProblemKind { kNS = 0, kAdvection = 1, kEnsemble = 2 };
+
+struct Problem;
+
+// a8: members of a batched ensemble and their launch geometry.
+struct EnsembleState {
+    std::vector<std::unique_ptr<Problem>> members;   // caller order
+    std::vector<int64_t> rec0;          // first state record of each member (caller order)
+    std::vector<double> dt;
+    std::vector<int64_t> n_steps;
+    std::vector<int> order;             // members by descending n_steps
+    std::vector<int64_t> blocks_before; // [n+1] stage blocks of the first k members in that order
+    std::vector<int64_t> rows_before;   // [n+1] ghost rows of the first k members in that order
+    DevBuf<unsigned char> descs;        // one block descriptor per stage block
+    int64_t total_records = 0, total_nodes = 0;
+    int active_members = 0;             // launch geometry of the captured graph
+};
 
 struct GhostPlan {
-    int64_t n_ghost = 0;
+    int64_t n_ghost = 0;         // ghost rows in the layout
+    int64_t rows = 0;            // ghost rows processed per fill (active prefix)
     int n_comp = 0;
     int n_class = 0;
     int npad = 0;                // stencil slots per wall row, padded to 8
     int field_class[4] = {0, 0, 0, 0};
     DevBuf<int32_t> gidx;        // [n_ghost][npad] owner-stencil node per slot
     DevBuf<unsigned char> gw;    // [F][n_ghost][npad] T: BC weights, zero on ghosts
-    DevBuf<int32_t> owner;       // [n_ghost]
+    DevBuf<int32_t> owner;       // [n_ghost] state record of each row's wall node
     DevBuf<unsigned char> tb;    // [n_ghost] 1 if the owner is a bottom/top node
     DevBuf<int32_t> pos;         // [n_ghost] position of ghost row in component order
-    DevBuf<int32_t> at;          // [n_ghost] ghost row at each position
+    DevBuf<int64_t> grec;        // [n_ghost] state record of the ghost at each position
     DevBuf<int32_t> comp_of;     // [n_ghost] component of each position
     DevBuf<int64_t> comp_start;  // [n_comp + 1] first position of each component
     DevBuf<int64_t> inv_off;     // [n_class][n_comp] offset of each inverse block
@@ -85,6 +103,7 @@ struct Problem {
     std::vector<cudaEvent_t> rhs_ev;   // [2 * 4 * graph_steps] when recording
 
     float weight_build_ms = 0.f, ghost_setup_ms = 0.f;
+    std::unique_ptr<EnsembleState> ens;
 
     size_t tsize() const { return precision == 64 ? 8 : 4; }
     ~Problem();
@@ -98,6 +117,14 @@ void pack_operators(Problem &pb);
 void build_ghost_plan(Problem &pb, const int32_t *kind_host, const int32_t *owner_host);
 void enqueue_ghost_fill(Problem &pb, void *U, cudaStream_t s);
 void minmax(Problem &pb, const void *U, double *out);
+void build_ns(Problem &pb, const rbf_ns_params &prm, const double *x, const double *z, int64_t n_prog,
+              int64_t n_all, const int32_t *kind, const int32_t *ghost_owner, void *stream, bool with_scratch);
+void alloc_scratch(Problem &pb);
+void enqueue_ens_step(Problem &pb, double dt_unused, void *U, cudaStream_t s, bool rec, int step);
+void build_ensemble(Problem &pb, const rbf_ns_params &common, int n, const rbf_ens_member *mem, const double *x,
+                    const double *z, const int32_t *kind, const int32_t *owner, void *stream);
+void run_ensemble(Problem &pb, int64_t max_steps, void *U);
+double ensemble_node_updates(const Problem &pb, int64_t max_steps);
 
 }  // namespace rbf
 

@@ -214,73 +214,96 @@ def hilbert_order(x: np.ndarray, z: np.ndarray, bits: int = 16) -> np.ndarray:
     return np.argsort(d, kind="stable")
 
 
-def poisson_disk_nodes(x0: float, x1: float, z0: float, z1: float, h: float, seed: int = 1) -> NodeSet:
-    """Quasi-uniformly scattered nodes (Sec. 5.1) by seeded Bridson sampling.
+def _poisson_disk_points(x0, W, z0, H, r, rng, periodic_x=False, rounds=60):
+    """Near-maximal Poisson-disk sample with minimum distance r in the box
+    [x0, x0+W) x [z0, z0+H], by parallel dart throwing on a background grid
+    of cells of size about r/sqrt(2) (at most one point per cell).  Cells are
+    processed in 9 colour classes (i mod 3, j mod 3): proposals of one class
+    are at least two cells apart and cannot conflict with each other, so a
+    whole class is tested against the accepted points at once.  With a
+    periodic x the column count is a multiple of 3, so the classes also stay
+    apart across the seam."""
+    cs = r / math.sqrt(2.0)
+    if periodic_x:
+        ncx = max(3, 3 * int(math.floor(W / cs) // 3))
+    else:
+        ncx = max(1, int(math.ceil(W / cs)))
+    ncz = max(1, int(math.ceil(H / cs)))
+    cw, ch = W / ncx, H / ncz
+    px = np.full((ncz, ncx), np.nan)
+    pz = np.full((ncz, ncx), np.nan)
+    offs = [(dj, di) for dj in range(-2, 3) for di in range(-2, 3) if (dj, di) != (0, 0)]
+    total = 0
+    for _ in range(rounds):
+        added = 0
+        for cj in range(3):
+            for ci in range(3):
+                sub_x = px[cj::3, ci::3]
+                if sub_x.size == 0:
+                    continue
+                empty = np.isnan(sub_x)
+                if not empty.any():
+                    continue
+                # neighbours through a 2-cell NaN (or periodic) border
+                Px = np.pad(px, 2, constant_values=np.nan)
+                Pz = np.pad(pz, 2, constant_values=np.nan)
+                if periodic_x:
+                    Px[2:-2, :2] = px[:, -2:] - W
+                    Px[2:-2, -2:] = px[:, :2] + W
+                    Pz[2:-2, :2] = pz[:, -2:]
+                    Pz[2:-2, -2:] = pz[:, :2]
+                nr, nc = sub_x.shape
+                jj = (cj + 3 * np.arange(nr))[:, None]
+                ii = (ci + 3 * np.arange(nc))[None, :]
+                cx = x0 + (ii + rng.uniform(size=(nr, nc))) * cw
+                cz = z0 + (jj + rng.uniform(size=(nr, nc))) * ch
+                ok = empty.copy()
+                for dj, di in offs:
+                    qx = Px[2 + cj + dj::3, 2 + ci + di::3][:nr, :nc]
+                    qz = Pz[2 + cj + dj::3, 2 + ci + di::3][:nr, :nc]
+                    ok &= ~((cx - qx) ** 2 + (cz - qz) ** 2 < r * r)   # NaN compares False
+                px[cj::3, ci::3] = np.where(ok, cx, sub_x)
+                pz[cj::3, ci::3] = np.where(ok, cz, pz[cj::3, ci::3])
+                added += int(ok.sum())
+        total += added
+        if added <= max(1, total // 500):   # saturated: further darts rarely land
+            break
+    m = ~np.isnan(px)
+    return px[m], pz[m]
 
-    Walls carry evenly spaced boundary nodes (spacing h); interior samples keep
-    a minimum distance r_min from each other and at least h/2 from the walls.
-    r_min is chosen so that sqrt(area / N) is close to h.  Each boundary node
-    gets one ghost at distance h outside along the wall normal (corner nodes
-    belong to the bottom/top walls).  Nodes are ordered along a Hilbert curve.
+
+def poisson_disk_nodes(x0: float, x1: float, z0: float, z1: float, h: float, seed: int = 1,
+                       periodic_x: bool = False) -> NodeSet:
+    """Quasi-uniformly scattered nodes (Sec. 5.1) by seeded Poisson-disk sampling.
+
+    Walls carry evenly spaced boundary nodes (spacing h): top and bottom, and
+    left and right unless ``periodic_x``.  Interior samples keep a minimum
+    distance r_min = 0.83 h from each other (so that sqrt(area / N) is close to
+    h) and at least h/2 from the walls.  Each wall node gets one ghost at
+    distance h outside along the wall normal; corner nodes belong to the
+    bottom/top walls.  Nodes are ordered along a Hilbert curve.
     """
     rng = np.random.default_rng(seed)
     W, H = x1 - x0, z1 - z0
     nbx = int(round(W / h))
     nbz = int(round(H / h))
-    bx = x0 + np.arange(nbx + 1) * (W / nbx)
-    bz = z0 + np.arange(1, nbz) * (H / nbz)
-    wall_x = np.concatenate([bx, bx, np.full(bz.shape, x0), np.full(bz.shape, x1)])
-    wall_z = np.concatenate([np.full(bx.shape, z0), np.full(bx.shape, z1), bz, bz])
-    wall_k = np.concatenate([np.full(bx.shape, KIND_BOTTOM), np.full(bx.shape, KIND_TOP),
-                             np.full(bz.shape, KIND_LEFT), np.full(bz.shape, KIND_RIGHT)])
-    # Bridson sampling in the shrunken box with min distance r_min
-    r_min = 0.93 * h
-    cell = r_min / math.sqrt(2.0)
-    gx0, gz0 = x0 + 0.5 * h, z0 + 0.5 * h
-    gW, gH = W - h, H - h
-    ncx, ncz = int(math.ceil(gW / cell)) + 1, int(math.ceil(gH / cell)) + 1
-    grid = -np.ones((ncz, ncx), np.int64)
-    pts = []
-    active = []
-
-    def fits(px, pz):
-        ci, cj = int((px - gx0) / cell), int((pz - gz0) / cell)
-        for jj in range(max(cj - 2, 0), min(cj + 3, ncz)):
-            for ii in range(max(ci - 2, 0), min(ci + 3, ncx)):
-                q = grid[jj, ii]
-                if q >= 0:
-                    qx, qz = pts[q]
-                    if (qx - px) ** 2 + (qz - pz) ** 2 < r_min * r_min:
-                        return False
-        return True
-
-    p0 = (gx0 + rng.uniform() * gW, gz0 + rng.uniform() * gH)
-    pts.append(p0)
-    grid[int((p0[1] - gz0) / cell), int((p0[0] - gx0) / cell)] = 0
-    active.append(0)
-    k_try = 30
-    while active:
-        a = active[rng.integers(len(active))]
-        ax, az = pts[a]
-        placed = False
-        rr = r_min * np.sqrt(rng.uniform(1.0, 4.0, k_try))
-        th = rng.uniform(0.0, 2.0 * math.pi, k_try)
-        for t in range(k_try):
-            px, pz = ax + rr[t] * math.cos(th[t]), az + rr[t] * math.sin(th[t])
-            if not (gx0 <= px <= gx0 + gW and gz0 <= pz <= gz0 + gH):
-                continue
-            if fits(px, pz):
-                pts.append((px, pz))
-                grid[int((pz - gz0) / cell), int((px - gx0) / cell)] = len(pts) - 1
-                active.append(len(pts) - 1)
-                placed = True
-                break
-        if not placed:
-            active.remove(a)
-    ip = np.array(pts)
-    x = np.concatenate([ip[:, 0], wall_x])
-    z = np.concatenate([ip[:, 1], wall_z])
-    kind = np.concatenate([np.zeros(ip.shape[0], np.int32), wall_k.astype(np.int32)])
+    if periodic_x:
+        bx = x0 + np.arange(nbx) * (W / nbx)
+        wall_x = np.concatenate([bx, bx])
+        wall_z = np.concatenate([np.full(bx.shape, z0), np.full(bx.shape, z1)])
+        wall_k = np.concatenate([np.full(bx.shape, KIND_BOTTOM), np.full(bx.shape, KIND_TOP)])
+        ix, iz = _poisson_disk_points(x0, W, z0 + 0.5 * h, H - h, 0.83 * h, rng, periodic_x=True)
+    else:
+        bx = x0 + np.arange(nbx + 1) * (W / nbx)
+        bz = z0 + np.arange(1, nbz) * (H / nbz)
+        wall_x = np.concatenate([bx, bx, np.full(bz.shape, x0), np.full(bz.shape, x1)])
+        wall_z = np.concatenate([np.full(bx.shape, z0), np.full(bx.shape, z1), bz, bz])
+        wall_k = np.concatenate([np.full(bx.shape, KIND_BOTTOM), np.full(bx.shape, KIND_TOP),
+                                 np.full(bz.shape, KIND_LEFT), np.full(bz.shape, KIND_RIGHT)])
+        ix, iz = _poisson_disk_points(x0 + 0.5 * h, W - h, z0 + 0.5 * h, H - h, 0.83 * h, rng)
+    x = np.concatenate([ix, wall_x])
+    z = np.concatenate([iz, wall_z])
+    kind = np.concatenate([np.zeros(ix.shape[0], np.int32), wall_k.astype(np.int32)])
     perm = hilbert_order(x, z)
     x, z, kind = x[perm], z[perm], kind[perm]
     n_prog = x.shape[0]
@@ -292,7 +315,7 @@ def poisson_disk_nodes(x0: float, x1: float, z0: float, z1: float, h: float, see
     return NodeSet(x=np.concatenate([x, gx]), z=np.concatenate([z, gz]), n_prog=n_prog, kind=kind,
                    ghost_owner=bidx.astype(np.int32),
                    src=np.concatenate([np.arange(n_prog), -np.ones(bidx.shape[0], np.int64)]).astype(np.int32),
-                   period_x=0.0, h=h, layout="scattered", domain=(x0, x1, z0, z1))
+                   period_x=W if periodic_x else 0.0, h=h, layout="scattered", domain=(x0, x1, z0, z1))
 
 
 # ----------------------------------------------------------------------------
@@ -350,3 +373,51 @@ def perturbed_density_current(nodes: NodeSet, seed: int) -> np.ndarray:
     xc = 0.0 + 4000.0 * rng.uniform(-0.1, 0.1)
     zc = 3000.0 * (1.0 + rng.uniform(-0.1, 0.1))
     return density_current_state(nodes, amp=a, xc=xc, zc=zc)
+
+
+# ----------------------------------------------------------------------------
+# Batched ensembles of density-current runs of uneven size
+# ----------------------------------------------------------------------------
+
+# (stencil size, polynomial degree) choices of ensemble members; every pair is
+# linearly stable at dt = h/400 with the hyperviscosity of Sec. 5.3 (n = 21
+# is not: the RK4 amplification of its worst mode exceeds 1.09)
+ENSEMBLE_STENCILS = ((31, 3), (37, 4), (45, 4), (56, 5), (75, 5))
+
+
+@dataclasses.dataclass
+class EnsembleMember:
+    nodes: NodeSet
+    n: int          # stencil size
+    l: int          # polynomial degree
+    dt: float
+    n_steps: int
+    U0: np.ndarray  # float64 [4, n_all] initial state
+    seed: int
+
+
+def density_current_member(h, layout, n, l, seed, t_end=900.0):
+    """One ensemble member: the density current at spacing h on a Cartesian,
+    hexagonal or scattered layout, with the seeded +/-10% perturbation of its
+    amplitude and centre, stepped with dt = h/400 (Sec. 6.3 table) to t_end."""
+    if layout == "scattered":
+        nodes = poisson_disk_nodes(-25600.0, 25600.0, 0.0, 6400.0, h, seed=seed, periodic_x=True)
+    else:
+        nodes = density_current_nodes(h, layout=layout)
+    dt = h / 400.0
+    return EnsembleMember(nodes=nodes, n=n, l=l, dt=dt, n_steps=int(round(t_end / dt)),
+                          U0=perturbed_density_current(nodes, seed), seed=seed)
+
+
+def ensemble_members(n_runs=256, seed=0, spacings=(50.0, 100.0, 200.0, 400.0),
+                     layouts=("cart", "hex", "scattered"), stencils=ENSEMBLE_STENCILS, t_end=900.0):
+    """Seeded draw of ensemble members: spacing, layout, stencil size and
+    perturbation of each run."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(n_runs):
+        h = float(spacings[rng.integers(len(spacings))])
+        layout = str(layouts[rng.integers(len(layouts))])
+        n, l = stencils[rng.integers(len(stencils))]
+        out.append(density_current_member(h, layout, n, l, seed=seed * 100003 + r, t_end=t_end))
+    return out

@@ -41,6 +41,11 @@ class AdvParams(C.Structure):
                 ("hv_p", C.c_int32), ("precision", C.c_int32), ("gamma", C.c_double), ("period_T", C.c_double)]
 
 
+class EnsMember(C.Structure):
+    _fields_ = [("n_prog", C.c_int64), ("n_all", C.c_int64), ("n_sten", C.c_int32), ("poly_l", C.c_int32),
+                ("period_x", C.c_double), ("gamma", C.c_double), ("dt", C.c_double), ("n_steps", C.c_int64)]
+
+
 class Info(C.Structure):
     _fields_ = [("n_prog", C.c_int64), ("n_all", C.c_int64), ("n_ghost", C.c_int64), ("n_fields", C.c_int32),
                 ("precision", C.c_int32), ("n_sten", C.c_int32), ("threads_per_node", C.c_int32),
@@ -64,6 +69,10 @@ SIGNATURES = [
     ("rbf_build_weights", C.c_int, [_P, _P, _I64, _P, _I64, _I32, _D, _I32, _I32, _I32, _P, _I32, _P, _P]),
     ("rbf_ns_create", C.c_int, [C.POINTER(_P), C.POINTER(NSParams), _P, _P, _I64, _I64, _P, _P, _P]),
     ("rbf_adv_create", C.c_int, [C.POINTER(_P), C.POINTER(AdvParams), _P, _P, _I64, _I64, _P, _P, _P, _P]),
+    ("rbf_ens_create", C.c_int, [C.POINTER(_P), C.POINTER(NSParams), _I32, C.POINTER(EnsMember), _P, _P, _P, _P,
+                                 _P]),
+    ("rbf_ens_run", C.c_int, [_P, _I64, _P]),
+    ("rbf_ens_node_updates", C.c_int, [_P, _I64, C.POINTER(C.c_double)]),
     ("rbf_rhs", C.c_int, [_P, _D, _P, _P]),
     ("rbf_rk4_step", C.c_int, [_P, _D, _D, _P]),
     ("rbf_run", C.c_int, [_P, _D, _D, _I64, _P]),
@@ -295,3 +304,57 @@ def state_tensor(U, precision, device="cuda"):
 def fields(t):
     """Node-major tensor [n, F] -> field-major float64 numpy array [F, n]."""
     return t.detach().cpu().double().numpy().T.copy()
+
+
+class Ensemble(Problem):
+    """A batched ensemble (a8): members' node-major records concatenated."""
+
+    def __init__(self, handle, members, precision):
+        n_all = sum(m.nodes.n_all for m in members)
+        n_prog = sum(m.nodes.n_prog for m in members)
+        super().__init__(handle, 4, n_prog, n_all, precision, "ensemble")
+        self.members = members
+        self.rec0 = np.cumsum([0] + [m.nodes.n_all for m in members])[:-1]
+
+    @property
+    def state_shape(self):
+        return (self.n_all, 4)
+
+    def state(self, device="cuda"):
+        """Initial state of every member, node-major, concatenated."""
+        return state_tensor(np.concatenate([m.U0 for m in self.members], axis=1), self.precision, device)
+
+    def member_fields(self, U, r):
+        """Field-major float64 [4, n_all] of member r."""
+        m = self.members[r]
+        return fields(U[self.rec0[r]:self.rec0[r] + m.nodes.n_all])
+
+    def run(self, max_steps, U):
+        _check(lib().rbf_ens_run(self._h, int(max_steps), _ptr(self._state(U))))
+        return U
+
+    def node_updates(self, max_steps=-1):
+        v = C.c_double()
+        _check(lib().rbf_ens_node_updates(self._h, int(max_steps), C.byref(v)))
+        return v.value
+
+
+def ensemble_problem(members, precision=32, p=7, hv_k=3, mu=75.0, gamma_c=2.0 ** -6, theta_bar=inp.THETA_BAR):
+    """Batched ensemble of density-current members (inputs.EnsembleMember)."""
+    _torch()
+    common = NSParams(n_sten=37, phs_p=p, poly_l=4, hv_k=hv_k, hv_p=p, precision=precision, threads_per_node=0,
+                      reserved=0, period_x=0.0, mu=mu, gamma=0.0, theta_bar=theta_bar, g=inp.G, cp=inp.CP,
+                      cv=inp.CV, rd=inp.RD)
+    arr = (EnsMember * len(members))()
+    for r, m in enumerate(members):
+        arr[r] = EnsMember(n_prog=m.nodes.n_prog, n_all=m.nodes.n_all, n_sten=m.n, poly_l=m.l,
+                           period_x=m.nodes.period_x, gamma=hyperviscosity_gamma(gamma_c, m.nodes.h, hv_k),
+                           dt=m.dt, n_steps=m.n_steps)
+    x = np.ascontiguousarray(np.concatenate([m.nodes.x for m in members]), np.float64)
+    z = np.ascontiguousarray(np.concatenate([m.nodes.z for m in members]), np.float64)
+    kind = np.ascontiguousarray(np.concatenate([m.nodes.kind for m in members]), np.int32)
+    owner = np.ascontiguousarray(np.concatenate([m.nodes.ghost_owner for m in members]), np.int32)
+    h = C.c_void_p()
+    _check(lib().rbf_ens_create(C.byref(h), C.byref(common), len(members), arr, _host_ptr(x), _host_ptr(z),
+                                _host_ptr(kind), _host_ptr(owner), _stream()))
+    return Ensemble(h, members, precision)

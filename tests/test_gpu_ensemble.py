@@ -1,0 +1,81 @@
+"""a8: batched ensembles of uneven runs (GPU, through the C ABI).
+
+* FP64: every member after its own number of RK4 steps (of its own dt)
+  matches the oracle run of that member: relative l2 < 1e-10 per field (the
+  FP64 single-problem bound, the members being independent problems).
+* FP32: every member is bitwise equal to the same member stepped alone as a
+  single problem with the same lanes per node (same operand order, same
+  ghost solve), so batching changes nothing but the launch geometry.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle.ns import NSOracle  # noqa: E402
+from paper_1509_02615_gb300 import inputs as inp  # noqa: E402
+from paper_1509_02615_gb300 import rbffd  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1509_02615_gb300 import _build
+    _build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def _members(t_scale=1.0):
+    spec = [(800.0, "hex", 37, 4, 30.0), (400.0, "cart", 31, 3, 12.0), (800.0, "scattered", 45, 4, 20.0),
+            (400.0, "hex", 56, 5, 8.0), (800.0, "cart", 75, 5, 16.0)]
+    return [inp.density_current_member(h, lay, n, l, seed=17 + i, t_end=t * t_scale)
+            for i, (h, lay, n, l, t) in enumerate(spec)]
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_ensemble_fp64_matches_oracle_per_member():
+    mem = _members()
+    ens = rbffd.ensemble_problem(mem, precision=64)
+    U = ens.state()
+    ens.run(-1, U)
+    ens.sync()
+    assert ens.node_updates() == sum(m.nodes.n_prog * m.n_steps for m in mem)
+    for r, m in enumerate(mem):
+        o = NSOracle(m.nodes, n=m.n, l=m.l)
+        ref = o.run(m.U0, 0.0, m.dt, m.n_steps)
+        got = ens.member_fields(U, r)
+        P = m.nodes.n_prog
+        errs = [rel(got[f, :P], ref[f, :P]) for f in range(4)]
+        print(f"member {r} ({m.nodes.layout}, h={m.nodes.h:g}, n={m.n}, steps={m.n_steps}) rel l2", errs)
+        assert max(errs) < 1e-10, (r, errs)
+
+
+def test_ensemble_fp32_equals_members_stepped_alone():
+    mem = _members()
+    ens = rbffd.ensemble_problem(mem, precision=32)
+    G = ens.info()["threads_per_node"]
+    U = ens.state()
+    ens.run(-1, U)
+    ens.sync()
+    for r, m in enumerate(mem):
+        pb = rbffd.ns_problem(m.nodes, precision=32, n=m.n, l=m.l, threads_per_node=G)
+        V = rbffd.state_tensor(m.U0, 32)
+        pb.run(0.0, m.dt, m.n_steps, V)
+        pb.sync()
+        a = U[ens.rec0[r]:ens.rec0[r] + m.nodes.n_prog]
+        assert torch.equal(a, V[:m.nodes.n_prog]), r
+
+
+def test_ensemble_partial_run_counts():
+    mem = _members(t_scale=0.5)
+    ens = rbffd.ensemble_problem(mem, precision=32)
+    assert ens.node_updates(3) == sum(m.nodes.n_prog * min(3, m.n_steps) for m in mem)
+    U = ens.state()
+    ens.run(3, U)
+    mm = ens.minmax(U)
+    assert np.all(np.isfinite(mm))
