@@ -213,6 +213,80 @@ int rbf_ens_run(rbf_problem *pb, int64_t max_steps, void *U);
 /* Node updates (prognostic nodes x steps) that rbf_ens_run(max_steps) performs. */
 int rbf_ens_node_updates(const rbf_problem *pb, int64_t max_steps, double *out);
 
+/* ---- a9: learned tendency correction ----------------------------------------
+ * The paper has no learned component; this is a small per-node MLP that
+ * corrects coarse runs of the method.  Features of node i: the stencil
+ * differences U_f(x_j) - U_f(x_i) of the four fields over the n - 1
+ * non-centre nodes of i's stencil divided by per-field scales s_in
+ * (field-major order, 4 (n - 1) values), then the node's own four values
+ * divided by s_own (4 values).  Network: f(x) = h2 W3 + b3 with
+ * h1 = tanh(x W1 + b1), h2 = tanh(h1 W2 + b2), width 64, BF16 weights, FP32
+ * accumulation; y = f(x) - f(0), so a locally uniform state gets no
+ * correction.  Output: delta_f = y_f s_out[f] (y clipped to [-4, 4] when
+ * applied), added as dt * delta after each coarse RK4 step (Dirichlet
+ * components excluded).
+ * Parameters (FP32 master copy, flat): W1 [4(n-1)+4][64], b1 [64], W2 [64][64],
+ * b2 [64], W3 [64][4], b3 [4].  Data sets: states [n_runs][n_snap][n_all][4]
+ * FP32 (ghosts filled), targets [n_runs][n_snap-1][n_prog][4] FP32.
+ */
+typedef struct rbf_mlp rbf_mlp;
+
+/* MLP bound to a coarse Navier-Stokes problem (its stencils and flags); the
+ * problem must outlive the MLP.  Weights start at zero: set them. */
+int rbf_mlp_create(rbf_mlp **out, rbf_problem *coarse, void *stream);
+int rbf_mlp_n_params(const rbf_mlp *m, int64_t *out);
+/* host float [n_params]; also refreshes the BF16 copy and resets Adam */
+int rbf_mlp_set_params(rbf_mlp *m, const float *params);
+int rbf_mlp_get_params(const rbf_mlp *m, float *params);
+/* host float [12]: s_in[4], s_out[4], s_own[4] (all > 0) */
+int rbf_mlp_set_scales(rbf_mlp *m, const float *scales);
+int rbf_mlp_get_scales(const rbf_mlp *m, float *scales);
+/* scales = root mean squares of the differences, targets and values of a data set (device) */
+int rbf_mlp_fit_scales(rbf_mlp *m, const float *states, const float *targets, int64_t n_runs, int64_t n_snap);
+/*
+ * Loss (mean over samples and outputs of (y - target/s_out)^2, y unclipped) and its
+ * gradient for a given batch: samples device int64 [batch][2] (target index
+ * k in [0, n_runs (n_snap-1)), node i); grad_host float [n_params].
+ */
+int rbf_mlp_grad(rbf_mlp *m, const float *states, const float *targets, int64_t n_runs, int64_t n_snap,
+                 const int64_t *samples, int32_t batch, float *grad_host, float *loss_host);
+/* iters Adam steps on random batches (seeded on the device); loss_host [iters] or NULL */
+int rbf_mlp_train(rbf_mlp *m, const float *states, const float *targets, int64_t n_runs, int64_t n_snap,
+                  int64_t iters, int32_t batch, float lr, uint64_t seed, float *loss_host);
+/* delta [n_prog][4] for a state U [n_all][4] whose ghosts are filled (device) */
+int rbf_mlp_forward(rbf_mlp *m, const void *U, void *delta);
+/*
+ * n_steps corrected coarse steps: ghost fill, delta = MLP(U), RK4 step,
+ * U_f += alpha[f] * dt * delta_f (alpha: host double [4], each >= 0; all
+ * zero is the uncorrected solver).
+ * A non-finite delta is skipped (the uncorrected step is kept) and counted
+ * in *n_fallback (host, optional).  Synchronous.
+ */
+int rbf_learned_run(rbf_mlp *m, double t0, double dt, int64_t n_steps, const double *alpha, void *U,
+                    int64_t *n_fallback);
+int rbf_mlp_destroy(rbf_mlp *m);
+/*
+ * Restriction by injection (device): for e < n_map, record
+ * (e / block_records) * block_stride + e % block_records of dst takes record
+ * map[e] of src (node-major records of 4 fields; precisions 32 or 64).
+ */
+int rbf_restrict(const void *src, int32_t src_precision, const int64_t *map, int64_t n_map, void *dst,
+                 int32_t dst_precision, int64_t block_records, int64_t block_stride, void *stream);
+/*
+ * Weighted restriction (device): dst record of entry e (placed as in
+ * rbf_restrict) = sum over q < m of w[e][q] * src record idx[e][q];
+ * idx int64 [n_map][m], w double [n_map][m]; dst FP32.
+ */
+int rbf_restrict_weighted(const void *src, int32_t src_precision, const int64_t *idx, const double *w, int32_t m,
+                          int64_t n_map, float *dst, int64_t block_records, int64_t block_stride, void *stream);
+/* The ghost solve of Sec. 5.2 alone: fills the ghost records of U (device). */
+int rbf_fill_ghosts(rbf_problem *pb, void *U);
+/*
+ * Training targets of a data set: target (r, k) = (state (r, k+1) -
+ * one coarse RK4 step from state (r, k)) / dt.  FP32 problem; device arrays.
+ */
+int rbf_mlp_targets(rbf_problem *pb, const float *states, int64_t n_runs, int64_t n_snap, double dt, float *targets);
+
 /*
  * a4+a5(+a6)  Right-hand side at time t.
  *   U     device, FP64 or FP32 per the problem's precision:

@@ -56,14 +56,17 @@ class NodeSet:
         return self.n_all - self.n_prog
 
 
-def _lattice_rows(layout, x0, x1, z0, z1, h, periodic_x):
+def _lattice_rows(layout, x0, x1, z0, z1, h, periodic_x, rows=None):
     """Row positions and per-row x coordinates of a lattice covering the box.
 
     Hexagonal rows are fitted to the domain height: R = round(H / (h*sqrt(3)/2))
     intervals of dz = H / R, odd rows shifted by half a column (Sec. 5.1).
+    ``rows`` overrides R (nested lattices).
     """
     W, H = x1 - x0, z1 - z0
-    if layout == "hex":
+    if rows is not None:
+        nint = int(rows)
+    elif layout == "hex":
         nint = max(1, int(round(H / (h * math.sqrt(3.0) / 2.0))))
     elif layout == "cart":
         nint = max(1, int(round(H / h)))
@@ -91,7 +94,7 @@ def _row_x(layout, r, x0, ncol, dx, periodic_x):
 
 
 def lattice_nodes(layout: str, x0: float, x1: float, z0: float, z1: float, h: float,
-                  periodic_x: bool = True) -> NodeSet:
+                  periodic_x: bool = True, rows: int = None) -> NodeSet:
     """Cartesian or hexagonal lattice with one ghost row below and above.
 
     Each top and bottom wall node gets one ghost one row spacing outside it,
@@ -99,7 +102,7 @@ def lattice_nodes(layout: str, x0: float, x1: float, z0: float, z1: float, h: fl
     walls as well and get one ghost column outside, continuing the row.  Corner
     nodes belong to the top or bottom wall.
     """
-    nint, dz, ncol, dx = _lattice_rows(layout, x0, x1, z0, z1, h, periodic_x)
+    nint, dz, ncol, dx = _lattice_rows(layout, x0, x1, z0, z1, h, periodic_x, rows)
     xs, zs, kinds = [], [], []
     gx, gz, gown = [], [], []
     for r in range(nint + 1):
@@ -421,3 +424,58 @@ def ensemble_members(n_runs=256, seed=0, spacings=(50.0, 100.0, 200.0, 400.0),
         n, l = stencils[rng.integers(len(stencils))]
         out.append(density_current_member(h, layout, n, l, seed=seed * 100003 + r, t_end=t_end))
     return out
+
+
+# ----------------------------------------------------------------------------
+# Nested lattices for the learned coarse-grid correction
+# ----------------------------------------------------------------------------
+
+def nested_density_current(h_coarse: float, ratio: int):
+    """Coarse and fine hexagonal density-current lattices with every coarse node
+    on a fine node: the coarse lattice keeps its fitted row count R_c, the
+    fine one uses ratio * R_c rows and ratio times the columns (an odd coarse
+    row's half-column shift is ratio/2 fine columns, so ratio is even).
+    Returns (coarse, fine, restrict) with restrict[i] the fine node of coarse
+    prognostic node i (restriction by injection)."""
+    if ratio % 2:
+        raise ValueError("the nesting ratio must be even")
+    coarse = density_current_nodes(h_coarse)
+    Rc = len(np.unique(coarse.z[:coarse.n_prog])) - 1   # coarse row intervals
+    fine = lattice_nodes("hex", -25600.0, 25600.0, 0.0, 6400.0, h_coarse / ratio, True, rows=ratio * Rc)
+    key = {(round(a, 6), round(b, 6)): j for j, (a, b) in enumerate(zip(fine.x[:fine.n_prog], fine.z[:fine.n_prog]))}
+    restrict = np.array([key[(round(a, 6), round(b, 6))]
+                         for a, b in zip(coarse.x[:coarse.n_prog], coarse.z[:coarse.n_prog])], np.int64)
+    return coarse, fine, restrict
+
+
+def restriction_average(coarse: NodeSet, fine: NodeSet, inject: np.ndarray, radius: float, sigma: float):
+    """Low-pass restriction from fine to coarse prognostic nodes: a Gaussian
+    average (width sigma) over the fine prognostic nodes within ``radius`` of
+    each coarse node (minimum image in periodic x), weights normalised to 1.
+    Returns (idx [n_c, m], w [n_c, m]) padded with zero weights."""
+    P = fine.period_x
+    xf, zf = fine.x[:fine.n_prog], fine.z[:fine.n_prog]
+    rows_i, rows_w = [], []
+    for c in range(coarse.n_prog):
+        dx = xf - coarse.x[c]
+        if P > 0:
+            dx = np.where(dx > 0.5 * P, dx - P, np.where(dx < -0.5 * P, dx + P, dx))
+        d2 = dx * dx + (zf - coarse.z[c]) ** 2
+        sel = np.nonzero(d2 <= radius * radius)[0]
+        w = np.exp(-0.5 * d2[sel] / (sigma * sigma))
+        rows_i.append(sel)
+        rows_w.append(w / w.sum())
+    m = max(len(r) for r in rows_i)
+    idx = np.zeros((coarse.n_prog, m), np.int64)
+    wt = np.zeros((coarse.n_prog, m))
+    for c, (ii, ww) in enumerate(zip(rows_i, rows_w)):
+        idx[c, :len(ii)] = ii
+        idx[c, len(ii):] = inject[c]
+        wt[c, :len(ii)] = ww
+    return idx, wt
+
+
+def learned_correction_seeds(n_seeds=64, seed=5):
+    """Seeds of the perturbed density currents of the learned-correction data
+    set; the last eighth are held out for testing."""
+    return [int(seed * 1000 + s) for s in range(n_seeds)]

@@ -73,6 +73,22 @@ SIGNATURES = [
                                  _P]),
     ("rbf_ens_run", C.c_int, [_P, _I64, _P]),
     ("rbf_ens_node_updates", C.c_int, [_P, _I64, C.POINTER(C.c_double)]),
+    ("rbf_mlp_create", C.c_int, [C.POINTER(_P), _P, _P]),
+    ("rbf_mlp_n_params", C.c_int, [_P, C.POINTER(C.c_int64)]),
+    ("rbf_mlp_set_params", C.c_int, [_P, _P]),
+    ("rbf_mlp_get_params", C.c_int, [_P, _P]),
+    ("rbf_mlp_set_scales", C.c_int, [_P, _P]),
+    ("rbf_mlp_get_scales", C.c_int, [_P, _P]),
+    ("rbf_mlp_fit_scales", C.c_int, [_P, _P, _P, _I64, _I64]),
+    ("rbf_mlp_grad", C.c_int, [_P, _P, _P, _I64, _I64, _P, _I32, _P, _P]),
+    ("rbf_mlp_train", C.c_int, [_P, _P, _P, _I64, _I64, _I64, _I32, C.c_float, C.c_uint64, _P]),
+    ("rbf_mlp_forward", C.c_int, [_P, _P, _P]),
+    ("rbf_learned_run", C.c_int, [_P, _D, _D, _I64, _P, _P, C.POINTER(C.c_int64)]),
+    ("rbf_mlp_destroy", C.c_int, [_P]),
+    ("rbf_restrict", C.c_int, [_P, _I32, _P, _I64, _P, _I32, _I64, _I64, _P]),
+    ("rbf_restrict_weighted", C.c_int, [_P, _I32, _P, _P, _I32, _I64, _P, _I64, _I64, _P]),
+    ("rbf_fill_ghosts", C.c_int, [_P, _P]),
+    ("rbf_mlp_targets", C.c_int, [_P, _P, _I64, _I64, _D, _P]),
     ("rbf_rhs", C.c_int, [_P, _D, _P, _P]),
     ("rbf_rk4_step", C.c_int, [_P, _D, _D, _P]),
     ("rbf_run", C.c_int, [_P, _D, _D, _I64, _P]),
@@ -358,3 +374,100 @@ def ensemble_problem(members, precision=32, p=7, hv_k=3, mu=75.0, gamma_c=2.0 **
     _check(lib().rbf_ens_create(C.byref(h), C.byref(common), len(members), arr, _host_ptr(x), _host_ptr(z),
                                 _host_ptr(kind), _host_ptr(owner), _stream()))
     return Ensemble(h, members, precision)
+
+
+# ---- a9: learned tendency correction ----------------------------------------------
+
+class Mlp:
+    """The learned correction's network, bound to a coarse NS problem."""
+
+    def __init__(self, coarse: Problem):
+        _torch()
+        self.coarse = coarse
+        h = C.c_void_p()
+        _check(lib().rbf_mlp_create(C.byref(h), coarse._h, _stream()))
+        self._h = h
+        n = C.c_int64()
+        _check(lib().rbf_mlp_n_params(self._h, C.byref(n)))
+        self.n_params = n.value
+
+    def set_params(self, params):
+        a = np.ascontiguousarray(params, np.float32)
+        assert a.size == self.n_params
+        _check(lib().rbf_mlp_set_params(self._h, _host_ptr(a)))
+
+    def params(self):
+        a = np.zeros(self.n_params, np.float32)
+        _check(lib().rbf_mlp_get_params(self._h, _host_ptr(a)))
+        return a
+
+    def set_scales(self, scales):
+        a = np.ascontiguousarray(scales, np.float32)
+        _check(lib().rbf_mlp_set_scales(self._h, _host_ptr(a)))
+
+    def scales(self):
+        a = np.zeros(12, np.float32)
+        _check(lib().rbf_mlp_get_scales(self._h, _host_ptr(a)))
+        return a
+
+    def fit_scales(self, states, targets, n_runs, n_snap):
+        _check(lib().rbf_mlp_fit_scales(self._h, _ptr(states), _ptr(targets), n_runs, n_snap))
+
+    def grad(self, states, targets, n_runs, n_snap, samples):
+        g = np.zeros(self.n_params, np.float32)
+        loss = np.zeros(1, np.float32)
+        _check(lib().rbf_mlp_grad(self._h, _ptr(states), _ptr(targets), n_runs, n_snap, _ptr(samples),
+                                  samples.shape[0], _host_ptr(g), _host_ptr(loss)))
+        return float(loss[0]), g
+
+    def train(self, states, targets, n_runs, n_snap, iters, batch=4096, lr=2e-3, seed=0):
+        loss = np.zeros(max(iters, 1), np.float32)
+        _check(lib().rbf_mlp_train(self._h, _ptr(states), _ptr(targets), n_runs, n_snap, iters, batch, float(lr),
+                                   int(seed), _host_ptr(loss)))
+        return loss[:iters]
+
+    def forward(self, U, delta=None):
+        if delta is None:
+            delta = _torch().empty((self.coarse.n_prog, 4), dtype=U.dtype, device="cuda")
+        _check(lib().rbf_mlp_forward(self._h, _ptr(U), _ptr(delta)))
+        return delta
+
+    def run(self, t0, dt, n_steps, U, alpha=(1.0, 1.0, 1.0, 1.0)):
+        """Corrected coarse run (U_f += alpha_f dt delta_f after each step);
+        returns the number of skipped (non-finite) corrections."""
+        nf = C.c_int64()
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(alpha, np.float64), (4,)))
+        _check(lib().rbf_learned_run(self._h, float(t0), float(dt), int(n_steps), _host_ptr(a), _ptr(U),
+                                     C.byref(nf)))
+        return nf.value
+
+    def close(self):
+        if self._h:
+            _check(lib().rbf_mlp_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fill_ghosts(pb: Problem, U):
+    _check(lib().rbf_fill_ghosts(pb._h, _ptr(U)))
+    return U
+
+
+def restrict(src, src_precision, index_map, dst, dst_precision, block_records, block_stride):
+    _check(lib().rbf_restrict(_ptr(src), src_precision, _ptr(index_map), index_map.numel(), _ptr(dst),
+                              dst_precision, int(block_records), int(block_stride), _stream()))
+
+
+def restrict_weighted(src, src_precision, idx, w, dst, block_records, block_stride):
+    _check(lib().rbf_restrict_weighted(_ptr(src), src_precision, _ptr(idx), _ptr(w), idx.shape[1], idx.shape[0],
+                                       _ptr(dst), int(block_records), int(block_stride), _stream()))
+
+
+def mlp_targets(pb: Problem, states, n_runs, n_snap, dt, targets):
+    _check(lib().rbf_mlp_targets(pb._h, _ptr(states), int(n_runs), int(n_snap), float(dt), _ptr(targets)))
+    return targets
