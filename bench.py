@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--threads-per-node", type=int, default=0, help="0 = autotuned")
     ap.add_argument("--ens-runs", type=int, default=256, help="ensemble members (0 = skip the batched case)")
     ap.add_argument("--ens-steps", type=int, default=40, help="timed global RK4 steps of the ensemble")
+    ap.add_argument("--learned", type=int, default=1, help="1 = measure the learned coarse-grid correction")
+    ap.add_argument("--learned-coarse", type=float, default=400.0)
+    ap.add_argument("--learned-ratio", type=int, default=4)
+    ap.add_argument("--learned-seeds", type=int, default=16)
     ap.add_argument("--large-h", type=float, default=25.0,
                     help="spacing of the HBM-roofline case (0 = skip); its working set exceeds L2")
     return ap.parse_args()
@@ -252,6 +256,79 @@ def ensemble_case(torch, args):
     return out
 
 
+def learned_case(torch, args):
+    """Learned coarse-grid correction: coarse hexagonal runs corrected by the MLP,
+    against the restricted fine FP64 reference at 900 s (held-out seeds), with
+    the uncorrected coarse and 2x-finer runs beside it."""
+    from paper_1509_02615_gb300 import inputs as inp
+    from paper_1509_02615_gb300 import learned
+    from paper_1509_02615_gb300 import rbffd
+    hc, ratio, ns = args.learned_coarse, args.learned_ratio, args.learned_seeds
+    n_train, n_val = int(round(ns * 0.625)), int(round(ns * 0.1875))
+    seeds = inp.learned_correction_seeds(ns, seed=1)
+    t0 = time.perf_counter()
+    ds = learned.build_dataset(hc, ratio, seeds, 900.0)
+    t_data = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mlp, loss = learned.train(ds, n_train, iters=3000, batch=4096, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    alpha, scores = learned.select_alpha(ds, mlp, range(n_train, n_train + n_val))
+    test = list(range(n_train + n_val, ns))
+    err_plain = learned.run_errors(ds, mlp, test, (0.0, 0.0, 0.0, 0.0))
+    err_learned = learned.run_errors(ds, mlp, test, alpha)
+    steps = ds.n_snap - 1
+    nc = ds.coarse_nodes.n_prog
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    V = ds.states[test[0], 0].clone()
+    e0.record()
+    mlp.run(0.0, ds.dt_c, steps, V, alpha=alpha)
+    e1.record()
+    e1.synchronize()
+    ms_learned = e0.elapsed_time(e1)
+    V = ds.states[test[0], 0].clone()
+    ds.coarse.run(0.0, ds.dt_c, steps, V)
+    e0.record()
+    ds.coarse.run(0.0, ds.dt_c, steps, V)
+    e1.record()
+    e1.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    # uncorrected runs at half the coarse spacing (FP64), restricted the same way
+    coarse_nodes, mid, rmap = inp.nested_density_current(hc, 2)
+    aidx, aw = inp.restriction_average(coarse_nodes, mid, rmap, radius=hc, sigma=0.5 * hc)
+    aidx_t = torch.as_tensor(aidx, device="cuda")
+    aw_t = torch.as_tensor(aw, device="cuda")
+    pb_mid = rbffd.ns_problem(mid, precision=64)
+    err_mid = []
+    ms_mid = 0.0
+    for r in test:
+        U = rbffd.state_tensor(inp.perturbed_density_current(mid, seeds[r]), 64)
+        e0.record()
+        pb_mid.run(0.0, hc / 800.0, 2 * steps, U)
+        e1.record()
+        e1.synchronize()
+        ms_mid += e0.elapsed_time(e1)
+        out = torch.zeros((coarse_nodes.n_all, 4), dtype=torch.float32, device="cuda")
+        rbffd.restrict_weighted(U, 64, aidx_t, aw_t, out, nc, coarse_nodes.n_all)
+        err_mid.append(learned.rel_l2(out[:nc], ds.states[r, -1, :nc]))
+    pb_mid.close()
+    out = {"workload": f"density current, hexagonal {hc:g} m coarse ({nc} nodes), MLP trained on {hc / ratio:g} m FP64 "
+                       f"runs restricted to the coarse nodes ({n_train} train / {n_val} validation / {len(test)} test "
+                       f"seeds), t = 900 s",
+           "selected_alpha": alpha, "validation_scores": [[sc, list(a)] for sc, a in scores],
+           "rel_l2_test": {"fields": ["u", "w", "theta'", "pi'"],
+                           "uncorrected_coarse_fp32": [float(v) for v in err_plain],
+                           "learned_coarse_fp32": [float(v) for v in err_learned],
+                           f"uncorrected_{hc / 2:g}m_fp64": [float(v) for v in np.mean(err_mid, axis=0)]},
+           "node_updates_per_s": {"learned_coarse_fp32": nc * steps / (ms_learned / 1e3),
+                                  "uncorrected_coarse_fp32": nc * steps / (ms_plain / 1e3),
+                                  f"uncorrected_{hc / 2:g}m_fp64": mid.n_prog * 2 * steps * len(test) / (ms_mid / 1e3),
+                                  "fine_reference_fp64_batched": ds.fine_node_updates / ds.fine_seconds},
+           "final_training_loss": float(np.mean(loss[-50:])),
+           "seconds": {"data": t_data, "train": t_train}}
+    mlp.close()
+    return out
+
+
 def cpu_baseline(h, budget_s=12.0):
     """FP64 oracle on a 1/8-width periodic strip of the same workload (same
     spacing, stencils, operators and boundary treatment): node-RHS/s."""
@@ -383,6 +460,9 @@ def main():
     batched = None
     if args.ens_runs > 0:
         batched = ensemble_case(torch, args)
+    learned_form = None
+    if args.learned:
+        learned_form = learned_case(torch, args)
 
     base = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -401,7 +481,8 @@ def main():
                 "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
                 "gpu_launches": info["launches_per_step"] * args.steps,
                 "setup": {"weight_build_ms": info["weight_build_ms"], "ghost_setup_ms": info["ghost_setup_ms"]},
-                "fp64": fp64, "roofline_large": large, "batched": batched, "cpu_baseline": base,
+                "fp64": fp64, "roofline_large": large, "batched": batched, "learned": learned_form,
+                "cpu_baseline": base,
                 "state_minmax": {"theta_min": mm[2, 0], "w_min": mm[1, 0], "w_max": mm[1, 1]}}
         print(json.dumps(line), flush=True)
     pb.close()
