@@ -1,0 +1,58 @@
+"""The five workloads of this package: node sets, method parameters, initial
+states, time steps and end times (synthetic, seeded; the paper's cases are
+closed-form, so no data set is involved).
+
+  advection        scalar transport in the deformational shear flow on the
+                   unit square (Sec. 6.1 method; flow, bell and T = 5 of the
+                   task), Cartesian 64 x 64 + 4 reflected layers, r^7 + deg 4,
+                   n = 37, -gamma Delta^4 from r^9, dt = T/1000, FP64
+  density_current  Sec. 6.3 at hexagonal 100 m, r^7 + deg 4, n = 37, Delta^3,
+                   mu = 75, dt = 0.25 s to 900 s
+  bubble           warm bubble (+2 K cos^2, R = 2 km at (10, 2) km) in a
+                   walled [0, 20] x [0, 10] km box, Poisson-disk nodes at 25 m,
+                   r^9 + deg 5, n = 56, Delta^3 from r^9, mu = 10,
+                   dt = 1/16 s to 1000 s, FP64 weights in FP32
+  ensemble         256 density-current members (inputs.ensemble_members)
+  learned          400 m coarse runs corrected by an MLP trained on fine runs
+                   (learned.py)
+"""
+from __future__ import annotations
+
+import dataclasses
+
+from . import inputs as inp
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    nodes: inp.NodeSet
+    params: dict          # keyword arguments of rbffd.ns_problem / advection_problem
+    U0: object            # float64 [F, n_all] (advection: [n_prog])
+    dt: float
+    n_steps: int
+
+
+def advection(m: int = 64) -> Workload:
+    nodes = inp.unit_square_mirrored(m)
+    U0 = inp.cosine_bell(nodes.x[:nodes.n_prog], nodes.z[:nodes.n_prog])
+    return Workload("advection", nodes, dict(n=37, p=7, l=4, hv_k=4, hv_p=9, gamma_c=2.0 ** -14, T=5.0), U0,
+                    5.0 / 1000.0, 1000)
+
+
+def density_current(h: float = 100.0, layout: str = "hex") -> Workload:
+    nodes = inp.density_current_nodes(h, layout=layout)
+    return Workload("density_current", nodes, dict(n=37, p=7, l=4, hv_k=3, mu=75.0, gamma_c=2.0 ** -6),
+                    inp.density_current_state(nodes), h / 400.0, int(round(900.0 * 400.0 / h)))
+
+
+# Hyperviscosity constant of the bubble: with c = 2^-6 a corner of the
+# scattered walled node set has a linear mode outside RK4's stability region
+# (|R| = 1.009 per step at 500 m); c = 2^-4 damps it (|R| <= 1.00003).
+BUBBLE_GAMMA_C = 2.0 ** -4
+
+
+def bubble(h: float = 25.0, seed: int = 1, t_end: float = 1000.0) -> Workload:
+    nodes = inp.poisson_disk_nodes(0.0, 20000.0, 0.0, 10000.0, h, seed=seed)
+    return Workload("bubble", nodes, dict(n=56, p=9, l=5, hv_k=3, hv_p=9, mu=10.0, gamma_c=BUBBLE_GAMMA_C),
+                    inp.warm_bubble_state(nodes), h / 400.0, int(round(t_end * 400.0 / h)))
