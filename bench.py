@@ -64,6 +64,23 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value, world):
+    """Maximum of a per-rank float over all ranks (the whole job's time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units processed by all ranks divided by the (max-over-ranks) time."""
+    return units_per_rank * world / seconds
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -404,13 +421,8 @@ def main():
         # (the events also break the programmatic overlap of the launches)
         _, stage_ms = time_steps(torch, pb, U, dt, args.steps, 1, flush, True)
     torch.cuda.synchronize()
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    node_rhs = 4.0 * nodes.n_prog * args.steps * world
-    value = node_rhs / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(step_ms), world)
+    value = whole_job_rate(4.0 * nodes.n_prog * args.steps, world, total_ms / 1e3)
     mm = pb.minmax(U)   # fails loudly on NaN/Inf
 
     # roofline of the dominant kernel: the fused RHS + RK4 stage kernel
