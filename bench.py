@@ -89,9 +89,11 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(key=""):
+    """Hash of the sources of the kernel a profile key names."""
     h = hashlib.sha256()
-    for fn in ("ns.cu", "problem.cuh"):
+    files = ("persistent.cu", "problem.cuh") if key.startswith("persistent") else ("ns.cu", "problem.cuh")
+    for fn in files:
         with open(os.path.join(ROOT, "paper_1509_02615_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -107,7 +109,7 @@ def profiled_traffic(key):
     except (OSError, ValueError):
         return None
     e = d.get(key)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(key):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -414,27 +416,38 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    persistent = info["run_mode"] == 2
     with ClockSampler(local) as clk:
         step_ms, _ = time_steps(torch, pb, U, dt, args.steps, args.warmup, flush, False)
         torch.cuda.synchronize()
-        # same steps again with timing events around the four stage kernels
-        # (the events also break the programmatic overlap of the launches)
-        _, stage_ms = time_steps(torch, pb, U, dt, args.steps, 1, flush, True)
+        stage_ms = []
+        if not persistent:
+            # same steps again with timing events around the four stage kernels
+            # (the events also break the programmatic overlap of the launches)
+            _, stage_ms = time_steps(torch, pb, U, dt, args.steps, 1, flush, True)
     torch.cuda.synchronize()
     total_ms = max_over_ranks(sum(step_ms), world)
     value = whole_job_rate(4.0 * nodes.n_prog * args.steps, world, total_ms / 1e3)
     mm = pb.minmax(U)   # fails loudly on NaN/Inf
 
-    # roofline of the dominant kernel: the fused RHS + RK4 stage kernel
-    stage_avg_ms = float(np.mean(stage_ms)) / 4.0
-    bytes_per_launch = info["rhs_bytes_per_node"] * nodes.n_prog
-    achieved = bytes_per_launch / (stage_avg_ms / 1e3) / 1e9
-    key = f"ns_stage_fp{args.precision}_hex{int(args.h)}"
+    # roofline of the dominant kernel: the persistent kernel (one launch per
+    # step: 4 stages of algorithmic bytes) or the fused RHS + RK4 stage kernel
+    if persistent:
+        avg_ms = float(np.mean(step_ms))
+        bytes_per_launch = 4.0 * info["rhs_bytes_per_node"] * nodes.n_prog
+        kernel = "rk4_persistent"
+        share = 1.0
+    else:
+        avg_ms = float(np.mean(stage_ms)) / 4.0
+        bytes_per_launch = info["rhs_bytes_per_node"] * nodes.n_prog
+        kernel = "ns_stage_kernel"
+        share = float(np.sum(stage_ms) / np.sum(step_ms))
+    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
+    key = f"{'persistent' if persistent else 'ns_stage'}_fp{args.precision}_hex{int(args.h)}"
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": profiled_traffic(key), "kernel": "ns_stage_kernel",
-            "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": stage_avg_ms,
-            "stage_share_of_step": float(np.sum(stage_ms) / np.sum(step_ms)) if stage_ms else None,
-            "peak_source": f"{pk_kind} hbm_gbs"}
+            "frac": achieved / pk["hbm_gbs"], "traffic": profiled_traffic(key), "kernel": kernel,
+            "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
+            "kernel_share_of_step": share, "peak_source": f"{pk_kind} hbm_gbs"}
 
     # end to end through the C ABI on a pinned host state, copies included
     Uh = rbffd.state_tensor(U0, args.precision, device="cpu").pin_memory()
@@ -453,17 +466,24 @@ def main():
     if not args.no_fp64 and args.precision == 32:
         n64, pb64, _ = make_problem(args.h, 64)
         U64 = rbffd.state_tensor(U0, 64)
-        s64, k64 = time_steps(torch, pb64, U64, dt, max(20, args.steps // 4), args.warmup, flush, True)
         i64 = pb64.info()
+        n_t = max(20, args.steps // 4)
+        s64, _ = time_steps(torch, pb64, U64, dt, n_t, args.warmup, flush, False)
         t64 = float(sum(s64))
-        avg64 = float(np.mean(k64)) / 4.0
-        flops = i64["rhs_flops_per_node"] * n64.n_prog
+        if i64["run_mode"] == 2:      # one persistent launch per step
+            avg64 = t64 / len(s64)
+            flops = 4.0 * i64["rhs_flops_per_node"] * n64.n_prog
+        else:
+            _, k64 = time_steps(torch, pb64, U64, dt, n_t, 1, flush, True)
+            avg64 = float(np.mean(k64)) / 4.0
+            flops = i64["rhs_flops_per_node"] * n64.n_prog
         fp64 = {"value": 4.0 * n64.n_prog * len(s64) / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / len(s64),
                 "roofline": {"bound": "alu", "achieved": flops / (avg64 / 1e3) / 1e12, "peak": 1.25,
                              "unit": "TFLOP/s", "frac": flops / (avg64 / 1e3) / 1e12 / 1.25,
                              "peak_source": "nominal GB300 FP64 rate", "avg_launch_ms": avg64,
                              "hbm_GBps": i64["rhs_bytes_per_node"] * n64.n_prog / (avg64 / 1e3) / 1e9},
-                "threads_per_node": i64["threads_per_node"]}
+                "threads_per_node": i64["threads_per_node"],
+                "run_mode": "persistent" if i64["run_mode"] == 2 else "graph"}
         pb64.close()
 
     large = None
@@ -489,9 +509,11 @@ def main():
                            "dt_s": dt, "precision": f"fp{args.precision}",
                            "l2": "flushed between timed steps (512 MB write); working set ~31 MB",
                            "parallelism": "replicas" if world > 1 else "single GPU",
-                           "threads_per_node": info["threads_per_node"], "prefetch": info["prefetch"]},
+                           "threads_per_node": info["threads_per_node"], "prefetch": info["prefetch"],
+                           "run_mode": "persistent" if persistent else "graph",
+                           "persistent_lanes": info["persist_lanes"], "persistent_chunk": info["persist_chunk"]},
                 "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
-                "gpu_launches": info["launches_per_step"] * args.steps,
+                "gpu_launches": (1 if persistent else info["launches_per_step"]) * args.steps,
                 "setup": {"weight_build_ms": info["weight_build_ms"], "ghost_setup_ms": info["ghost_setup_ms"]},
                 "fp64": fp64, "roofline_large": large, "batched": batched, "learned": learned_form,
                 "cpu_baseline": base,

@@ -303,8 +303,46 @@ int rbf_rhs(rbf_problem *pb, double t, void *U, void *dUdt);
  */
 int rbf_rk4_step(rbf_problem *pb, double t, double dt, void *U);
 
-/* n_steps RK4 steps from t0, replayed from a captured CUDA graph. */
+/*
+ * n_steps RK4 steps from t0, in the problem's run mode (rbf_set_run_mode):
+ * replayed from a captured CUDA graph of the per-stage kernels, or one
+ * persistent cooperative launch for all steps.  Asynchronous on the
+ * problem's stream; rbf_sync reports a persistent launch that gave up.
+ */
 int rbf_run(rbf_problem *pb, double t0, double dt, int64_t n_steps, void *U);
+
+/*
+ * Run modes of rbf_run for Navier-Stokes problems.
+ *   RBF_RUN_GRAPH       ghost residual, ghost solve and fused stage kernels
+ *                       per stage, captured once and replayed as a graph.
+ *   RBF_RUN_PERSISTENT  one cooperative launch runs every step: one CTA per
+ *                       SM owns a contiguous slice of nodes, copies the
+ *                       records its stencils read into shared memory each
+ *                       stage, and grid barriers separate the ghost
+ *                       residual, ghost solve and stage phases (Sec. 5.2,
+ *                       Eqs. (uEq)-(piEq), RK4).  Results equal the graph
+ *                       mode's with the same lanes per node.  Available when
+ *                       every node fits one co-resident grid.
+ *   RBF_RUN_AUTO        time both on a zero state and keep the faster
+ *                       (done at creation when threads_per_node is 0).
+ * lanes: lanes per node of the persistent kernel (1, 2 or 4; 0 = fastest).
+ * Errors: RBF_E_ARG if the mode is unknown, the problem is not a
+ * Navier-Stokes problem, or RBF_RUN_PERSISTENT does not fit.
+ */
+#define RBF_RUN_AUTO 0
+#define RBF_RUN_GRAPH 1
+#define RBF_RUN_PERSISTENT 2
+int rbf_set_run_mode(rbf_problem *pb, int32_t mode, int32_t lanes);
+
+/*
+ * Bound on the polls of each grid-barrier wait of the persistent kernel
+ * (default 2^21, about a second).  When a wait runs out, that CTA raises an
+ * abort flag, every CTA leaves at its next barrier, the launch ends with the
+ * state partially updated, and the next rbf_sync (or rbf_run_host) returns
+ * RBF_E_TIMEOUT and clears the flag.  polls >= 0; 0 gives up at the first
+ * wait that is not already complete (used by the tests of that path).
+ */
+int rbf_set_spin_limit(rbf_problem *pb, int64_t polls);
 
 /*
  * End-to-end form of rbf_run on a HOST state: copies U_host to the device,
@@ -312,7 +350,10 @@ int rbf_run(rbf_problem *pb, double t0, double dt, int64_t n_steps, void *U);
  */
 int rbf_run_host(rbf_problem *pb, double t0, double dt, int64_t n_steps, void *U_host);
 
-/* Waits for the problem's stream; returns RBF_E_CUDA on an asynchronous fault. */
+/*
+ * Waits for the problem's stream; returns RBF_E_CUDA on an asynchronous
+ * fault and RBF_E_TIMEOUT if a persistent launch gave up a barrier wait.
+ */
 int rbf_sync(rbf_problem *pb);
 
 /*
@@ -331,11 +372,15 @@ typedef struct rbf_info {
     int32_t n_components;       /* independent ghost systems                */
     int32_t n_ghost_classes;    /* distinct ghost matrices per component    */
     int32_t prefetch;           /* 1: stage kernel holds operands in registers */
-    int32_t reserved;
+    int32_t run_mode;           /* RBF_RUN_GRAPH or RBF_RUN_PERSISTENT       */
     double weight_build_ms;     /* GPU time of stencils + weights + pack    */
     double ghost_setup_ms;      /* GPU time of the ghost inverses           */
     double rhs_bytes_per_node;  /* algorithmic HBM bytes of one RHS stage   */
     double rhs_flops_per_node;  /* arithmetic of one RHS stage              */
+    int32_t persist_lanes;      /* persistent kernel: lanes per node (0: none) */
+    int32_t persist_regs;       /* 1: it keeps its operands in registers    */
+    int32_t persist_chunk;      /* nodes per CTA                            */
+    int32_t persist_halo_max;   /* largest per-CTA record list              */
 } rbf_info;
 int rbf_get_info(const rbf_problem *pb, rbf_info *out);
 

@@ -133,6 +133,11 @@ void run(Problem &pb, double t0, double dt, int64_t n_steps, void *U) {
     RBF_REQUIRE(n_steps >= 0, "n_steps < 0");
     RBF_REQUIRE(std::isfinite(dt) && std::isfinite(t0), "non-finite time or step");
     if (n_steps == 0) return;
+    if (pb.run_mode == RBF_RUN_PERSISTENT && pb.ps.ready && !pb.record_rhs_events) {
+        // the equations are autonomous: t0 does not enter the launch
+        persistent_run(pb, dt, n_steps, U, pb.st);
+        return;
+    }
     const int chunk = (int)std::min<int64_t>(n_steps, pb.record_rhs_events ? 1 : 16);
     if (!pb.graph || pb.graph_U != U || pb.graph_dt != dt || pb.graph_steps != chunk) capture(pb, U, dt, chunk);
     cudaEvent_t ev;
@@ -152,6 +157,83 @@ void run(Problem &pb, double t0, double dt, int64_t n_steps, void *U) {
     RBF_CUDA(cudaEventRecord(ev, pb.cap));
     RBF_CUDA(cudaStreamWaitEvent(pb.st, ev, 0));
     cudaEventDestroy(ev);   // released once the recorded work completes
+}
+
+// Times `steps` RK4 steps of the current run mode on U (best of three).
+float time_run(Problem &pb, void *U, int steps) {
+    cudaEvent_t e0, e1;
+    RBF_CUDA(cudaEventCreate(&e0));
+    RBF_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    try {
+        run(pb, 0.0, 1e-3, steps, U);   // warm-up (and graph capture)
+        for (int rep = 0; rep < 3; ++rep) {
+            RBF_CUDA(cudaEventRecord(e0, pb.st));
+            run(pb, 0.0, 1e-3, steps, U);
+            RBF_CUDA(cudaEventRecord(e1, pb.st));
+            RBF_CUDA(cudaEventSynchronize(e1));
+            float t = 0.f;
+            RBF_CUDA(cudaEventElapsedTime(&t, e0, e1));
+            best = std::min(best, t);
+        }
+        persistent_check(pb);
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
+}
+
+// Run-mode autotuner: graph replay against the persistent kernel for each
+// lane count that fits, on a zero state; keeps the fastest.  lanes > 0
+// restricts the persistent candidates to that lane count.
+void choose_run_mode(Problem &pb, int mode, int lanes) {
+    RBF_REQUIRE(pb.kind == kNS, "run modes apply to Navier-Stokes problems");
+    RBF_REQUIRE(mode == RBF_RUN_AUTO || mode == RBF_RUN_GRAPH || mode == RBF_RUN_PERSISTENT,
+                "unknown run mode %d", mode);
+    RBF_REQUIRE(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4, "lanes must be 0, 1, 2 or 4");
+    if (mode == RBF_RUN_GRAPH) {
+        pb.run_mode = RBF_RUN_GRAPH;
+        return;
+    }
+    std::vector<int> cands;
+    if (lanes) cands.push_back(lanes);
+    else cands = {1, 2, 4};
+    const bool timing = mode == RBF_RUN_AUTO || cands.size() > 1;
+    const size_t bytes = (size_t)pb.F * pb.n_all * pb.tsize();
+    DevBuf<unsigned char> U(timing ? bytes : 0);
+    if (timing) RBF_CUDA(cudaMemsetAsync(U.p, 0, bytes, pb.st));
+    const int steps = 8;
+    float best = 1e30f;
+    int bestG = 0;
+    if (mode == RBF_RUN_AUTO) {
+        pb.run_mode = RBF_RUN_GRAPH;
+        best = time_run(pb, U.p, steps);
+        invalidate_graph(pb);
+    }
+    for (int G : cands) {
+        if (!persistent_plan(pb, G)) continue;
+        if (!timing) { bestG = G; break; }
+        pb.run_mode = RBF_RUN_PERSISTENT;
+        const float t = time_run(pb, U.p, steps);
+        if (t < best) { best = t; bestG = G; }
+    }
+    if (bestG == 0) {
+        pb.ps.ready = false;
+        pb.run_mode = RBF_RUN_GRAPH;
+        RBF_REQUIRE(mode == RBF_RUN_AUTO, "the persistent kernel does not fit this problem");
+        return;
+    }
+    if (!pb.ps.ready || pb.ps.G != bestG) persistent_plan(pb, bestG);
+    RBF_REQUIRE(pb.ps.ready, "persistent plan failed");
+    pb.run_mode = RBF_RUN_PERSISTENT;
+    // zero the stage buffers the timing runs wrote (ghost records included)
+    RBF_CUDA(cudaMemsetAsync(pb.S0.p, 0, pb.S0.bytes(), pb.st));
+    RBF_CUDA(cudaMemsetAsync(pb.S1.p, 0, pb.S1.bytes(), pb.st));
+    RBF_CUDA(cudaStreamSynchronize(pb.st));
 }
 
 }  // namespace
@@ -231,6 +313,7 @@ void build_ns(Problem &pb, const rbf_ns_params &prm, const double *x, const doub
     rbf::build_ghost_plan(pb, kind, ghost_owner);
     if (with_scratch) rbf::alloc_scratch(pb);
     rbf::choose_threads(pb, prm.threads_per_node);
+    if (with_scratch && prm.threads_per_node == 0) rbf::choose_run_mode(pb, RBF_RUN_AUTO, 0);
     RBF_CUDA(cudaStreamSynchronize(pb.st));
 }
 
@@ -359,6 +442,7 @@ int rbf_run_host(rbf_problem *h, double t0, double dt, int64_t n_steps, void *U_
         rbf::run(pb, t0, dt, n_steps, pb.host_state.p);
         RBF_CUDA(cudaMemcpyAsync(U_host, pb.host_state.p, bytes, cudaMemcpyDeviceToHost, pb.st));
         RBF_CUDA(cudaStreamSynchronize(pb.st));
+        rbf::persistent_check(pb);
     });
 }
 
@@ -367,6 +451,25 @@ int rbf_sync(rbf_problem *h) {
         RBF_REQUIRE(h, "null problem");
         RBF_CUDA(cudaStreamSynchronize(h->impl.st));
         RBF_CUDA(cudaStreamSynchronize(h->impl.cap));
+        rbf::persistent_check(h->impl);
+    });
+}
+
+int rbf_set_run_mode(rbf_problem *h, int32_t mode, int32_t lanes) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h, "null problem");
+        Problem &pb = h->impl;
+        RBF_CUDA(cudaStreamSynchronize(pb.st));
+        RBF_CUDA(cudaStreamSynchronize(pb.cap));
+        rbf::choose_run_mode(pb, mode, lanes);
+    });
+}
+
+int rbf_set_spin_limit(rbf_problem *h, int64_t polls) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h, "null problem");
+        RBF_REQUIRE(polls >= 0, "spin limit must be >= 0");
+        h->impl.ps.spin_limit = polls;
     });
 }
 
@@ -395,6 +498,13 @@ int rbf_get_info(const rbf_problem *h, rbf_info *out) {
         out->n_components = pb.gh.n_comp;
         out->n_ghost_classes = pb.gh.n_class;
         out->prefetch = pb.pf > 0 ? 1 : 0;
+        out->run_mode = pb.kind == rbf::kNS ? pb.run_mode : RBF_RUN_GRAPH;
+        if (pb.ps.ready) {
+            out->persist_lanes = pb.ps.G;
+            out->persist_regs = pb.ps.R > 0 ? 1 : 0;
+            out->persist_chunk = pb.ps.chunk;
+            out->persist_halo_max = pb.ps.halo_max;
+        }
         out->weight_build_ms = pb.weight_build_ms;
         out->ghost_setup_ms = pb.ghost_setup_ms;
         const double ts = (double)pb.tsize();

@@ -49,6 +49,31 @@ struct GhostPlan {
     DevBuf<unsigned char> res;   // T [F][n_ghost] residual b - W_I u_I - W_B u_B
 };
 
+// Persistent run mode: one cooperative launch runs all the steps of an
+// rbf_run (csrc/persistent.cu).  Its operators are packed for its own lane
+// count; each CTA's stencil records are listed once (its halo) and the
+// packed slots refer to positions in that list.
+struct PersistPlan {
+    bool ready = false;
+    int G = 0;                   // lanes per node
+    int R = 0;                   // operand vectors held in registers (0: read each stage)
+    int maxt = 0;                // thread limit of the kernel variant
+    int SLQ = 0, V = 0;          // packing of pw / lidx (as Problem::SLQ, V)
+    int chunk = 0;               // nodes per CTA
+    int threads = 0, grid = 0;
+    int halo_max = 0;
+    int64_t halo_total = 0;
+    size_t smem = 0;
+    DevBuf<unsigned char> pw;    // T [4][SLQ][n_prog][G][V]
+    DevBuf<uint16_t> lidx;       // [SLQ][n_prog][G][V] halo position of each slot
+    DevBuf<int32_t> hoff;        // [grid + 1]
+    DevBuf<int32_t> hlist;       // halo records of each CTA: its own nodes first
+    DevBuf<unsigned int> arrive; // barrier arrivals, monotone across launches
+    unsigned base = 0;           // its value when the next launch starts
+    DevBuf<int> abort;           // set when a barrier wait gives up (sticky until rbf_sync)
+    long long spin_limit = 1LL << 21;   // polls per barrier wait (about a second)
+};
+
 struct Problem {
     ProblemKind kind = kNS;
     cudaStream_t st = nullptr;    // caller's stream
@@ -102,6 +127,9 @@ struct Problem {
     bool record_rhs_events = false;
     std::vector<cudaEvent_t> rhs_ev;   // [2 * 4 * graph_steps] when recording
 
+    int run_mode = 1;             // RBF_RUN_GRAPH or RBF_RUN_PERSISTENT
+    PersistPlan ps;
+
     float weight_build_ms = 0.f, ghost_setup_ms = 0.f;
     std::unique_ptr<EnsembleState> ens;
 
@@ -125,6 +153,12 @@ void build_ensemble(Problem &pb, const rbf_ns_params &common, int n, const rbf_e
                     const double *z, const int32_t *kind, const int32_t *owner, void *stream);
 void run_ensemble(Problem &pb, int64_t max_steps, void *U);
 double ensemble_node_updates(const Problem &pb, int64_t max_steps);
+// Builds the persistent plan for G lanes per node; false if the problem does
+// not fit one co-resident launch (pb.ps.ready tells the same).
+bool persistent_plan(Problem &pb, int G);
+void persistent_run(Problem &pb, double dt, int64_t n_steps, void *U, cudaStream_t s);
+// RBF_E_TIMEOUT (and clears the flag) if a persistent launch gave up a wait.
+void persistent_check(Problem &pb);
 
 }  // namespace rbf
 

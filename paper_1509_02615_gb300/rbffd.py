@@ -50,9 +50,11 @@ class Info(C.Structure):
     _fields_ = [("n_prog", C.c_int64), ("n_all", C.c_int64), ("n_ghost", C.c_int64), ("n_fields", C.c_int32),
                 ("precision", C.c_int32), ("n_sten", C.c_int32), ("threads_per_node", C.c_int32),
                 ("slots", C.c_int32), ("launches_per_step", C.c_int32), ("n_components", C.c_int32),
-                ("n_ghost_classes", C.c_int32), ("prefetch", C.c_int32), ("reserved", C.c_int32),
+                ("n_ghost_classes", C.c_int32), ("prefetch", C.c_int32), ("run_mode", C.c_int32),
                 ("weight_build_ms", C.c_double), ("ghost_setup_ms", C.c_double),
-                ("rhs_bytes_per_node", C.c_double), ("rhs_flops_per_node", C.c_double)]
+                ("rhs_bytes_per_node", C.c_double), ("rhs_flops_per_node", C.c_double),
+                ("persist_lanes", C.c_int32), ("persist_regs", C.c_int32), ("persist_chunk", C.c_int32),
+                ("persist_halo_max", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -93,6 +95,8 @@ SIGNATURES = [
     ("rbf_rk4_step", C.c_int, [_P, _D, _D, _P]),
     ("rbf_run", C.c_int, [_P, _D, _D, _I64, _P]),
     ("rbf_run_host", C.c_int, [_P, _D, _D, _I64, _P]),
+    ("rbf_set_run_mode", C.c_int, [_P, _I32, _I32]),
+    ("rbf_set_spin_limit", C.c_int, [_P, _I64]),
     ("rbf_sync", C.c_int, [_P]),
     ("rbf_minmax", C.c_int, [_P, _P, _P]),
     ("rbf_get_info", C.c_int, [_P, C.POINTER(Info)]),
@@ -221,6 +225,15 @@ class Problem:
 
     def sync(self):
         _check(lib().rbf_sync(self._h))
+
+    RUN_MODES = {"auto": 0, "graph": 1, "persistent": 2}
+
+    def set_run_mode(self, mode, lanes=0):
+        """'graph', 'persistent' or 'auto' (see rbf_set_run_mode)."""
+        _check(lib().rbf_set_run_mode(self._h, self.RUN_MODES[mode], int(lanes)))
+
+    def set_spin_limit(self, polls):
+        _check(lib().rbf_set_spin_limit(self._h, int(polls)))
 
     def minmax(self, U):
         out = np.zeros((self.n_fields, 2))

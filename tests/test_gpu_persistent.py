@@ -1,0 +1,150 @@
+"""Persistent run mode: one cooperative launch runs every RK4 step of an
+rbf_run (ghost residuals, ghost solves and fused stages separated by grid
+barriers).  Checked against the graph mode (same lanes per node: the same
+operations in the same order, so bit-identical results), against the FP64
+oracle, and on its bounded-wait failure path.
+
+Tolerances: bitwise equality with the graph mode; FP64 against the oracle
+1e-11 relative l2 per field after the stated steps (the per-stage RHS
+parity bound of the graph mode, which these runs reproduce bit for bit).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle.ns import NSOracle  # noqa: E402
+from paper_1509_02615_gb300 import inputs as inp  # noqa: E402
+from paper_1509_02615_gb300 import rbffd  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1509_02615_gb300 import _build
+    _build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _both_modes(nodes, prec, G, dt, steps):
+    pb = rbffd.ns_problem(nodes, precision=prec, threads_per_node=G)
+    U0 = inp.density_current_state(nodes)
+    A = rbffd.state_tensor(U0, prec)
+    B = A.clone()
+    pb.set_run_mode("graph")
+    pb.run(0.0, dt, steps, A)
+    pb.set_run_mode("persistent", lanes=G)
+    info = pb.info()
+    assert info["run_mode"] == 2 and info["persist_lanes"] == G
+    pb.run(0.0, dt, steps, B)
+    pb.sync()
+    return pb, A, B, info
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("G", [1, 2, 4])
+def test_persistent_equals_graph_bitwise_400m(prec, G):
+    nodes = inp.density_current_nodes(400.0)
+    pb, A, B, info = _both_modes(nodes, prec, G, 1.0, 25)
+    print(f"FP{prec} G={G}: chunk {info['persist_chunk']}, halo {info['persist_halo_max']}, "
+          f"registers {info['persist_regs']}")
+    assert torch.equal(A, B)
+    pb.close()
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_persistent_equals_graph_bitwise_100m(prec):
+    """The 100 m hexagonal density current (38,400 nodes, 253 per CTA):
+    the launch configuration the measurements use."""
+    nodes = inp.density_current_nodes(100.0)
+    pb, A, B, info = _both_modes(nodes, prec, 1, 0.25, 40)
+    print(f"100 m FP{prec}: chunk {info['persist_chunk']}, halo {info['persist_halo_max']}, "
+          f"registers {info['persist_regs']}")
+    if prec == 32:
+        assert info["persist_regs"] == 1
+    assert torch.equal(A, B)
+    pb.close()
+
+
+def test_persistent_fp64_matches_oracle():
+    nodes = inp.density_current_nodes(400.0)
+    o = NSOracle(nodes)
+    U0 = inp.density_current_state(nodes)
+    ref = o.run(U0, 0.0, 1.0, 40)
+    pb = rbffd.ns_problem(nodes, precision=64, threads_per_node=2)
+    pb.set_run_mode("persistent")
+    U = rbffd.state_tensor(U0, 64)
+    pb.run(0.0, 1.0, 40, U)
+    pb.sync()
+    got = rbffd.fields(U)
+    P = nodes.n_prog
+    errs = [rel(got[f, :P], ref[f, :P]) for f in range(4)]
+    print("persistent FP64 vs oracle, 40 steps:", [f"{e:.2e}" for e in errs])
+    assert max(errs) < 1e-11
+
+
+def test_persistent_timeout_reports_and_recovers():
+    """A barrier wait that runs out (spin limit 0: the first CTA to arrive
+    gives up) ends the launch and rbf_sync reports RBF_E_TIMEOUT; with the
+    limit restored the same problem runs correctly."""
+    nodes = inp.density_current_nodes(400.0)
+    pb = rbffd.ns_problem(nodes, precision=32, threads_per_node=1)
+    pb.set_run_mode("persistent", lanes=1)
+    assert pb.info()["persist_chunk"] * 100 < nodes.n_prog   # many CTAs
+    U0 = inp.density_current_state(nodes)
+    U = rbffd.state_tensor(U0, 32)
+    pb.set_spin_limit(0)
+    pb.run(0.0, 1.0, 5, U)
+    with pytest.raises(rbffd.RBFError) as e:
+        pb.sync()
+    assert e.value.code == rbffd.RBF_E_TIMEOUT
+    pb.sync()   # the flag is cleared once reported
+    pb.set_spin_limit(1 << 21)
+    U = rbffd.state_tensor(U0, 32)
+    V = U.clone()
+    pb.run(0.0, 1.0, 5, U)
+    pb.set_run_mode("graph")
+    pb.run(0.0, 1.0, 5, V)
+    pb.sync()
+    assert torch.equal(U, V)
+
+
+def test_run_mode_arguments():
+    nodes = inp.density_current_nodes(800.0)
+    pb = rbffd.ns_problem(nodes, precision=32, threads_per_node=2)
+    with pytest.raises(rbffd.RBFError) as e:
+        pb.set_run_mode("persistent", lanes=3)
+    assert e.value.code == rbffd.RBF_E_ARG
+    with pytest.raises(rbffd.RBFError):
+        pb.set_spin_limit(-1)
+    adv = rbffd.advection_problem(inp.unit_square_mirrored(16), precision=64)
+    with pytest.raises(rbffd.RBFError) as e:
+        adv.set_run_mode("persistent")
+    assert e.value.code == rbffd.RBF_E_ARG
+
+
+def test_autotuned_mode_matches_graph_mode():
+    """Creation with threads_per_node = 0 picks lanes and run mode by timing;
+    whichever it picks, 40 FP32 steps agree with the graph mode to FP32
+    rounding (different lane splits sum in different orders)."""
+    nodes = inp.density_current_nodes(100.0)
+    pb = rbffd.ns_problem(nodes, precision=32)
+    info = pb.info()
+    print("autotuned:", {k: info[k] for k in ("threads_per_node", "prefetch", "run_mode", "persist_lanes")})
+    U0 = inp.density_current_state(nodes)
+    A = rbffd.state_tensor(U0, 32)
+    pb.run(0.0, 0.25, 40, A)
+    ref = rbffd.ns_problem(nodes, precision=32, threads_per_node=4)
+    B = rbffd.state_tensor(U0, 32)
+    ref.run(0.0, 0.25, 40, B)
+    pb.sync()
+    ref.sync()
+    a, b = rbffd.fields(A)[:, :nodes.n_prog], rbffd.fields(B)[:, :nodes.n_prog]
+    for f in range(4):
+        assert rel(a[f], b[f]) < 1e-5, (f, rel(a[f], b[f]))
