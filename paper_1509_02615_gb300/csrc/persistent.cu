@@ -1,31 +1,34 @@
 // a4 + a5 + a7 in one launch: a whole rbf_run (n_steps classical RK4 steps,
 // four stages each, the ghost solve of Sec. 5.2 before every stage) as one
-// cooperative kernel, for problems small enough that all their nodes fit one
-// co-resident grid (one CTA per SM).
+// cooperative kernel, for problems whose nodes fit one co-resident grid.
 //
-// Each CTA owns `chunk` consecutive nodes.  Every record its nodes' stencils
-// read is listed once per CTA (its halo: own nodes first, then the others in
-// index order), and the packed slots refer to positions in that list.  Per
-// stage a CTA copies its halo records into shared memory with one round of
-// independent L2 loads, then evaluates the fused right-hand side of
-// Eqs. (uEq)-(piEq) with every gather served from shared memory.  With
-// R > 0 a lane also keeps its packed operators (R 16-byte vectors of each
-// of the four weight blocks and of the halo positions) in registers for the
-// whole run; the step-start state U_n and the RK4 accumulator of its node
-// live in registers too.
+// Layout.  The prognostic nodes are split by recursive coordinate bisection
+// into one compact block per CTA.  Each CTA lists once every record its
+// nodes' stencils read (own nodes first, then the other records in index
+// order, then the ghosts it solves for itself); its packed operators refer
+// to positions in that list.  With R > 0 a lane keeps its operators (R
+// 16-byte vectors of each weight block and of list positions) in registers
+// for the whole run; U_n and the RK4 accumulator of its node live in
+// registers too.
 //
-// Phases of one stage, separated by grid barriers:
-//   A  ghost residuals b - W_I u_I - W_B u_B (8 lanes per wall row),
-//   B  ghost values u_G = W_G^{-1} r (one warp per class and position),
-//   C  halo copy, stencil sums, tendencies and the RK4 update.
-// The arithmetic of each phase (operand order, lane reductions, epilogue)
-// is that of the launch-per-phase kernels with the same lane count, so both
-// run modes give the same numbers.
+// Ghosts without a global phase.  The ghost values solve
+// W_G u_G = b - W_I u_I - W_B u_B (Sec. 5.2).  The rows of W_G^{-1} decay
+// exponentially along the wall (the wall rows couple only nearby ghosts), so
+// each row is kept where its entries exceed 2^-8 eps of the row's largest:
+// the dropped part is below the rounding of the kept sum.  A CTA whose
+// stencils read ghosts forms, from its shared-memory records, the residuals
+// of every wall row in those ghosts' bands, then the ghost values it needs
+// (4 lanes per ghost and operator class, every field of the class at once).
 //
-// Every barrier wait is bounded: after spin_limit polls a CTA raises the
-// abort flag; every other CTA leaves at its next barrier, the launch ends,
-// and the host reports RBF_E_TIMEOUT.  No wait can outlive the launch.
+// One stage per CTA: copy the listed records of the stage input into
+// shared memory (its own nodes' from registers, the others in one round of
+// independent L2 loads), solve its ghosts,
+// evaluate Eqs. (uEq)-(piEq) and the RK4 update for its nodes, write them,
+// and meet every other CTA at a grid barrier.  Every barrier wait is
+// bounded: after spin_limit polls a CTA raises the abort flag, every CTA
+// leaves at its next barrier, and the host reports RBF_E_TIMEOUT.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -110,8 +113,8 @@ __device__ __forceinline__ void st_relaxed(int *p, int v) {
 // Grid barrier with a bounded wait.  `target` counts the arrivals expected
 // so far (gridDim.x per barrier on top of the counter's value at launch; the
 // comparison tolerates wrap-around, so the counter is never reset between
-// launches).
-// Returns false if this or another CTA gave up; the caller then returns.
+// launches).  Returns false if this or another CTA gave up; the caller then
+// returns.
 __device__ bool grid_barrier(unsigned *arrive, int *abort, unsigned &target, long long limit) {
     __shared__ int s_ok;
     __syncthreads();
@@ -138,27 +141,36 @@ __device__ bool grid_barrier(unsigned *arrive, int *abort, unsigned &target, lon
     return s_ok != 0;
 }
 
+// Layout of one CTA's block (host-built, identical on both sides).
+struct CtaInfo {
+    int32_t list_off;   // first entry of its record list in hlist
+    int32_t n_own;      // own nodes (open the list)
+    int32_t n_load;     // records copied from the stage input every stage
+    int32_t n_list;     // plus the ghosts it solves (close the list)
+    int32_t n_rows;     // wall rows whose residuals it forms
+    int32_t n_gc;       // (ghost, operator class) pairs it solves
+    int32_t n_set;      // weight sets per wall row
+    int32_t n_coef;     // band coefficients of all its pairs
+    int64_t blob_off;   // byte offset of its constant block
+    int32_t blob_bytes;
+    int32_t o_rw, o_rinfo, o_gc, o_cidx, o_cval;   // sections of the block (row slots at 0)
+};
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
 template <class T>
 struct PArgs {
     T *U, *S0, *S1;                 // node-major records [n_all][4]
-    const T *pw;                    // [4][SLQ][n_prog][G][V]
-    const uint16_t *lidx;           // [SLQ][n_prog][G][V]
-    const int32_t *hoff, *hlist;
+    const T *pw;                    // [4][SLQ][lanes][G][V], lanes = grid * chunk
+    const uint16_t *lidx;           // [SLQ][lanes][G][V]
+    const int32_t *hlist;
+    const CtaInfo *cta;
+    const unsigned char *blob;
     const T *pibar;
     const unsigned char *flags;
-    int64_t n_prog, total;          // total = SLQ * n_prog * G * V
-    int SLQ, chunk;
-    // ghost systems (GhostPlan)
-    int64_t ng, rows;
-    int npad, n_comp, n_class;
-    const int32_t *gidx, *owner, *pos, *comp_of;
-    const T *gw, *inv;
-    T *res;
-    const unsigned char *tb;
-    const int64_t *comp_start, *inv_off, *grec;
-    int4 cls_fields;
+    int64_t lanes, total;           // total = SLQ * lanes * G * V
+    int SLQ, chunk, npad;
     T cp_tb2, gconst;
-    // tendencies and RK4
     T cp, g_over_tb, theta_bar, dpibar, rd_cv;
     T an0, an1, an2, bs0, bs1, bs2, bs3;
     int64_t n_steps;
@@ -168,7 +180,8 @@ struct PArgs {
     long long spin_limit;
 };
 
-constexpr int kRowLanes = 8;   // lanes per wall row (phase A), as the ghost kernels
+constexpr int kRowLanes = 8;    // lanes per wall row in the residuals, as the ghost kernels
+constexpr int kPairLanes = 4;   // lanes per (ghost, class) pair in the ghost values
 
 template <class T, int G, int R, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant__ PArgs<T> a) {
@@ -178,22 +191,31 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
     constexpr int V = P::V;
     constexpr bool DIFF = sizeof(T) == 4;   // FP32: difference form (self slot dropped)
     extern __shared__ __align__(16) unsigned char smem_raw[];
+
+    const CtaInfo ci = a.cta[blockIdx.x];
     T *halo = reinterpret_cast<T *>(smem_raw);
+    T *res = reinterpret_cast<T *>(smem_raw + align16((size_t)ci.n_list * 4 * sizeof(T)));
+    unsigned char *blob = reinterpret_cast<unsigned char *>(res) + align16((size_t)ci.n_rows * 4 * sizeof(T));
+    {
+        const int4 *src = reinterpret_cast<const int4 *>(a.blob + ci.blob_off);
+        int4 *dst = reinterpret_cast<int4 *>(blob);
+        for (int k = threadIdx.x; k < ci.blob_bytes / 16; k += blockDim.x) dst[k] = __ldg(src + k);
+    }
+    const uint16_t *ridx = reinterpret_cast<const uint16_t *>(blob);
+    const T *rw = reinterpret_cast<const T *>(blob + ci.o_rw);
+    const int32_t *rinfo = reinterpret_cast<const int32_t *>(blob + ci.o_rinfo);
+    const int4 *gcs = reinterpret_cast<const int4 *>(blob + ci.o_gc);
+    const uint16_t *cidx = reinterpret_cast<const uint16_t *>(blob + ci.o_cidx);
+    const T *cval = reinterpret_cast<const T *>(blob + ci.o_cval);
+    const int32_t *hl = a.hlist + ci.list_off;
 
-    const int c = blockIdx.x;
-    const int h0 = a.hoff[c], nh = a.hoff[c + 1] - h0;
-    const int64_t n0 = (int64_t)c * a.chunk;
-    const int cnt = (int)min((int64_t)a.chunk, a.n_prog - n0);
     const int li = threadIdx.x / G, g = threadIdx.x % G;
-    const bool live = li < cnt;
-    const int64_t i = live ? n0 + li : n0;   // idle lanes mirror the first node
-    const int self = live ? li : 0;          // own nodes open the halo list
-    const int lane = threadIdx.x & 31;
-    const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const bool live = li < ci.n_own;
+    const int self = live ? li : 0;            // idle lanes mirror the first node
+    const int64_t i = __ldg(hl + self);
 
-    const int64_t stride = a.n_prog * G;     // in vectors, between consecutive q
-    const int64_t off0 = i * G + g;
+    const int64_t stride = a.lanes * G;        // in vectors, between consecutive q
+    const int64_t off0 = ((int64_t)blockIdx.x * a.chunk + (li < a.chunk ? li : 0)) * G + g;
     const W *wx = reinterpret_cast<const W *>(a.pw);
     const W *wz = reinterpret_cast<const W *>(a.pw + a.total);
     const W *wd = reinterpret_cast<const W *>(a.pw + 2 * a.total);
@@ -223,28 +245,44 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
         un[0] = r0.u; un[1] = r0.w; un[2] = r0.t; un[3] = r0.p;
     }
     unsigned target = a.base;
+    T o4[4] = {0, 0, 0, 0};   // the node's latest stage output
 
     for (int64_t step = 0; step < a.n_steps; ++step) {
         for (int st = 0; st < 4; ++st) {
-            T *Uin = st == 0 ? a.U : st == 2 ? a.S1 : a.S0;
+            const T *Uin = st == 0 ? a.U : st == 2 ? a.S1 : a.S0;
             T *Uout = st == 0 ? a.S0 : st == 1 ? a.S1 : st == 2 ? a.S0 : a.U;
-            if (a.rows > 0) {
-                // ---- A: ghost residuals, all four fields per row -------------
+            // ---- the CTA's records of the stage input: its own nodes' from
+            // registers (it wrote them), the others through L2 ----------------
+            const bool first = step == 0 && st == 0;
+            if (!first && live && g == 0) sh_store(halo, li, Rec<T>{o4[0], o4[1], o4[2], o4[3]});
+#pragma unroll 4
+            for (int k = (first ? 0 : ci.n_own) + threadIdx.x; k < ci.n_load; k += blockDim.x)
+                sh_store(halo, k, ld_rec_cg(Uin, __ldg(hl + k)));
+            __syncthreads();
+            if (ci.n_rows > 0) {
+                // ---- residuals b - W_I u_I - W_B u_B of its wall rows -----------
+                // 8 lanes per row (unrolled so that a lane's loads overlap)
                 const int per = a.npad / kRowLanes;
-                for (int64_t e = gwarp * 32 + lane; e < ((a.rows * kRowLanes + 31) & ~(int64_t)31);
-                     e += nwarps * 32) {
-                    int64_t r = e / kRowLanes;
-                    const int ln = (int)(e % kRowLanes);
-                    const bool rl = r < a.rows;
-                    if (!rl) r = a.rows - 1;
+                const int nlr = (ci.n_rows * kRowLanes + 31) & ~31;
+                for (int e = threadIdx.x; e < nlr; e += blockDim.x) {
+                    int r = e / kRowLanes;
+                    const int ln = e % kRowLanes;
+                    const bool rl = r < ci.n_rows;
+                    if (!rl) r = ci.n_rows - 1;
+                    const int inf = rinfo[r];
+                    const T *w0 = rw + ((size_t)r * ci.n_set + ((inf >> 17) & 3)) * a.npad + ln;
+                    const T *w1 = rw + ((size_t)r * ci.n_set + ((inf >> 19) & 3)) * a.npad + ln;
+                    const T *w2 = rw + ((size_t)r * ci.n_set + ((inf >> 21) & 3)) * a.npad + ln;
+                    const T *w3 = rw + ((size_t)r * ci.n_set + ((inf >> 23) & 3)) * a.npad + ln;
+                    const uint16_t *rj = ridx + (size_t)r * a.npad + ln;
                     T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll 4
                     for (int t = 0; t < per; ++t) {
-                        const int64_t o = r * a.npad + ln + kRowLanes * t;
-                        const Rec<T> v = ld_rec_cg(Uin, __ldg(a.gidx + o));
-                        a0 += __ldg(a.gw + o) * v.u;
-                        a1 += __ldg(a.gw + a.ng * a.npad + o) * v.w;
-                        a2 += __ldg(a.gw + 2 * a.ng * a.npad + o) * v.t;
-                        a3 += __ldg(a.gw + 3 * a.ng * a.npad + o) * v.p;
+                        const Rec<T> v = sh_rec(halo, rj[kRowLanes * t]);
+                        a0 += w0[kRowLanes * t] * v.u;
+                        a1 += w1[kRowLanes * t] * v.w;
+                        a2 += w2[kRowLanes * t] * v.t;
+                        a3 += w3[kRowLanes * t] * v.p;
                     }
 #pragma unroll
                     for (int o = kRowLanes / 2; o > 0; o >>= 1) {
@@ -256,43 +294,46 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
                     if (rl && ln < 4) {
                         const T acc = ln == 0 ? a0 : ln == 1 ? a1 : ln == 2 ? a2 : a3;
                         T b = 0;
-                        if (ln == 3 && __ldg(a.tb + r)) {
+                        if (ln == 3 && (inf & (1 << 16))) {
                             // pi'_z = g theta' / (c_p theta_bar (theta_bar + theta')) at the wall node
-                            const T th = __ldcg(Uin + (int64_t)__ldg(a.owner + r) * 4 + 2);
+                            const T th = halo[(size_t)(inf & 0xffff) * 4 + 2];
                             b = a.gconst * th / (a.cp_tb2 + a.cp_tb2 / a.theta_bar * th);
                         }
-                        a.res[ln * a.ng + __ldg(a.pos + r)] = b - acc;
+                        res[ln * ci.n_rows + r] = b - acc;
                     }
                 }
-                if (!grid_barrier(a.arrive, a.abort, target, a.spin_limit)) return;
-                // ---- B: ghost values, one warp per (class, position) ---------
-                for (int64_t w = gwarp; w < (int64_t)a.n_class * a.rows; w += nwarps) {
-                    const int cls = (int)(w / a.rows);
-                    const int64_t q = w - (int64_t)cls * a.rows;
-                    const int cc = __ldg(a.comp_of + q);
-                    const int64_t s0 = __ldg(a.comp_start + cc);
-                    const int m = (int)(__ldg(a.comp_start + cc + 1) - s0);
-                    const int row = (int)(q - s0);
-                    const T *Ainv = a.inv + __ldg(a.inv_off + cls * a.n_comp + cc) + (int64_t)row * m;
-                    const int fm = cls == 0 ? a.cls_fields.x : cls == 1 ? a.cls_fields.y
-                                 : cls == 2 ? a.cls_fields.z : a.cls_fields.w;
-                    const int64_t rec = __ldg(a.grec + q);
+                __syncthreads();
+                // ---- ghost values from the banded inverse rows -------------------
+                // 4 lanes per (ghost, class) pair, every field of the class at once
+                const int npl = (ci.n_gc * kPairLanes + 31) & ~31;
+                for (int e = threadIdx.x; e < npl; e += blockDim.x) {
+                    const int k = e / kPairLanes, ln = e % kPairLanes;
+                    const int4 gc = gcs[k < ci.n_gc ? k : ci.n_gc - 1];   // position, field mask, first, count
+                    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+                    const uint16_t *cj = cidx + gc.z;
+                    const T *cv = cval + gc.z;
+#pragma unroll 4
+                    for (int j = ln; j < gc.w; j += kPairLanes) {
+                        const T c = cv[j];
+                        const int rr = cj[j];
+                        if (gc.y & 1) s0 += c * res[rr];
+                        if (gc.y & 2) s1 += c * res[ci.n_rows + rr];
+                        if (gc.y & 4) s2 += c * res[2 * ci.n_rows + rr];
+                        if (gc.y & 8) s3 += c * res[3 * ci.n_rows + rr];
+                    }
 #pragma unroll
-                    for (int f = 0; f < 4; ++f) {
-                        if (!(fm & (1 << f))) continue;
-                        const T *rr = a.res + f * a.ng + s0;
-                        T s = 0;
-                        for (int j = lane; j < m; j += 32) s += __ldg(Ainv + j) * __ldcg(rr + j);
-                        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                        if (lane == 0) Uin[rec * 4 + f] = s;
+                    for (int o = kPairLanes / 2; o > 0; o >>= 1) {
+                        s0 += __shfl_xor_sync(0xffffffffu, s0, o, kPairLanes);
+                        s1 += __shfl_xor_sync(0xffffffffu, s1, o, kPairLanes);
+                        s2 += __shfl_xor_sync(0xffffffffu, s2, o, kPairLanes);
+                        s3 += __shfl_xor_sync(0xffffffffu, s3, o, kPairLanes);
                     }
+                    if (k < ci.n_gc && ln < 4 && (gc.y & (1 << ln)))
+                        halo[(size_t)gc.x * 4 + ln] = ln == 0 ? s0 : ln == 1 ? s1 : ln == 2 ? s2 : s3;
                 }
-                if (!grid_barrier(a.arrive, a.abort, target, a.spin_limit)) return;
+                __syncthreads();
             }
-            // ---- C: halo copy, stencil sums, tendencies, RK4 update ----------
-            for (int h = threadIdx.x; h < nh; h += blockDim.x)
-                sh_store(halo, h, ld_rec_cg(Uin, __ldg(a.hlist + h0 + h)));
-            __syncthreads();
+            // ---- stencil sums, tendencies, RK4 update ----------------------------
             Rec<T> fi = {0, 0, 0, 0};
             if (DIFF) fi = sh_rec(halo, self);
             T ux = 0, uz = 0, ud = 0, wx_ = 0, wz_ = 0, wd_ = 0, tx = 0, tz = 0, td = 0, px = 0, pz = 0, ph = 0;
@@ -344,7 +385,6 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
             if (fl & 2) k[0] = 0;   // u = 0 held on left/right walls
             const T an = st == 0 ? a.an0 : st == 1 ? a.an1 : a.an2;
             const T bs = st == 0 ? a.bs0 : st == 1 ? a.bs1 : st == 2 ? a.bs2 : a.bs3;
-            T o4[4];
 #pragma unroll
             for (int f = 0; f < 4; ++f) {
                 const T kf = k[f];
@@ -371,8 +411,8 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
 
 // Kernel variants: (lanes per node, operand vectors held in registers,
 // thread limit).  The register variant covers FP32 stencils of up to 36
-// packed slots with one lane per node (255 registers, no spills); the others
-// read their operands each stage.
+// packed slots with one lane per node; the others read their operands each
+// stage.  Thread limits keep each variant within the register file.
 struct Variant {
     int G, R, maxt;
     void *fn;
@@ -382,8 +422,8 @@ template <class T>
 std::vector<Variant> variants() {
     if constexpr (sizeof(T) == 4) {
         return {{1, 9, 256, (void *)rk4_persistent<float, 1, 9, 256>},
-                {1, 0, 1024, (void *)rk4_persistent<float, 1, 0, 1024>},
-                {2, 0, 1024, (void *)rk4_persistent<float, 2, 0, 1024>},
+                {1, 0, 512, (void *)rk4_persistent<float, 1, 0, 512>},
+                {2, 0, 512, (void *)rk4_persistent<float, 2, 0, 512>},
                 {4, 0, 1024, (void *)rk4_persistent<float, 4, 0, 1024>}};
     } else {
         return {{1, 0, 512, (void *)rk4_persistent<double, 1, 0, 512>},
@@ -395,40 +435,22 @@ std::vector<Variant> variants() {
 template <class T>
 PArgs<T> pargs(Problem &pb, T *U, double dt, int64_t n_steps) {
     const PersistPlan &ps = pb.ps;
-    const GhostPlan &gh = pb.gh;
     PArgs<T> a{};
     a.U = U;
     a.S0 = (T *)pb.S0.p;
     a.S1 = (T *)pb.S1.p;
     a.pw = (const T *)ps.pw.p;
     a.lidx = ps.lidx.p;
-    a.hoff = ps.hoff.p;
     a.hlist = ps.hlist.p;
+    a.cta = (const CtaInfo *)ps.cta.p;
+    a.blob = ps.blob.p;
     a.pibar = (const T *)pb.pibar.p;
     a.flags = pb.flags.p;
-    a.n_prog = pb.n_prog;
-    a.total = (int64_t)ps.SLQ * pb.n_prog * ps.G * ps.V;
+    a.lanes = (int64_t)ps.grid * ps.chunk;
+    a.total = (int64_t)ps.SLQ * a.lanes * ps.G * ps.V;
     a.SLQ = ps.SLQ;
     a.chunk = ps.chunk;
-    a.ng = gh.n_ghost;
-    a.rows = gh.n_ghost > 0 ? gh.rows : 0;
-    a.npad = gh.npad;
-    a.n_comp = gh.n_comp;
-    a.n_class = gh.n_class;
-    a.gidx = gh.gidx.p;
-    a.owner = gh.owner.p;
-    a.pos = gh.pos.p;
-    a.comp_of = gh.comp_of.p;
-    a.gw = (const T *)gh.gw.p;
-    a.inv = (const T *)gh.inv.p;
-    a.res = (T *)gh.res.p;
-    a.tb = gh.tb.p;
-    a.comp_start = gh.comp_start.p;
-    a.inv_off = gh.inv_off.p;
-    a.grec = gh.grec.p;
-    int fields[4] = {0, 0, 0, 0};
-    for (int f = 0; f < 4; ++f) fields[gh.field_class[f]] |= 1 << f;
-    a.cls_fields = make_int4(fields[0], fields[1], fields[2], fields[3]);
+    a.npad = pb.gh.npad;
     a.cp_tb2 = (T)(pb.cp * pb.theta_bar * pb.theta_bar);
     a.gconst = (T)pb.g;
     a.cp = (T)pb.cp;
@@ -459,6 +481,41 @@ void *variant_fn(const PersistPlan &ps, int precision) {
     return nullptr;
 }
 
+// Recursive coordinate bisection: splits ids[lo, hi) into `parts` blocks of
+// equal size (+-1), cutting across the longer extent each time; ties by index.
+void bisect(std::vector<int32_t> &ids, size_t lo, size_t hi, int parts, const std::vector<double> &x,
+            const std::vector<double> &z, std::vector<std::pair<size_t, size_t>> &out) {
+    if (parts == 1) {
+        out.emplace_back(lo, hi);
+        return;
+    }
+    double x0 = 1e300, x1 = -1e300, z0 = 1e300, z1 = -1e300;
+    for (size_t k = lo; k < hi; ++k) {
+        x0 = std::min(x0, x[ids[k]]); x1 = std::max(x1, x[ids[k]]);
+        z0 = std::min(z0, z[ids[k]]); z1 = std::max(z1, z[ids[k]]);
+    }
+    const std::vector<double> &c = (x1 - x0 >= z1 - z0) ? x : z;
+    const int p1 = parts / 2;
+    const size_t mid = lo + (size_t)((double)(hi - lo) * p1 / parts + 0.5);
+    std::nth_element(ids.begin() + lo, ids.begin() + mid, ids.begin() + hi, [&](int32_t a, int32_t b) {
+        return c[a] < c[b] || (c[a] == c[b] && a < b);
+    });
+    bisect(ids, lo, mid, p1, x, z, out);
+    bisect(ids, mid, hi, parts - p1, x, z, out);
+}
+
+template <class V>
+std::vector<V> to_host(const DevBuf<V> &d) {
+    std::vector<V> h(d.n);
+    if (d.n) RBF_CUDA(cudaMemcpy(h.data(), d.p, d.bytes(), cudaMemcpyDeviceToHost));
+    return h;
+}
+
+void put(std::vector<unsigned char> &b, size_t at, const void *src, size_t bytes) {
+    if (b.size() < at + bytes) b.resize(at + bytes, 0);
+    if (bytes) memcpy(b.data() + at, src, bytes);
+}
+
 }  // namespace
 
 bool persistent_plan(Problem &pb, int G) {
@@ -471,11 +528,14 @@ bool persistent_plan(Problem &pb, int G) {
     RBF_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     if (!coop) return false;
     const int nsm = sm_count();
-    const int chunk = div_up(pb.n_prog, nsm);
+    const int64_t P = pb.n_prog;
+    const int grid = (int)std::min<int64_t>(nsm, P);
+    const int chunk = div_up(P, grid) + 1;   // bisection blocks differ by at most one node
     const int threads = div_up((int64_t)chunk * G, 32) * 32;
     if (threads > 1024) return false;
+    RBF_CUDA(cudaStreamSynchronize(pb.st));
 
-    // operators packed for G lanes, kept beside the launch-per-stage packing
+    // operators packed for G lanes (beside the launch-per-stage packing)
     const int G0 = pb.G, pf0 = pb.pf, SLQ0 = pb.SLQ, SL0 = pb.SL, V0 = pb.V;
     DevBuf<int32_t> pidx0 = std::move(pb.pidx);
     DevBuf<unsigned char> pw0 = std::move(pb.pw);
@@ -485,92 +545,298 @@ bool persistent_plan(Problem &pb, int G) {
         pb.G = G0; pb.pf = pf0; pb.SLQ = SLQ0; pb.SL = SL0; pb.V = V0;
     };
     std::vector<int32_t> hp;
+    std::vector<unsigned char> hw;
+    int SLQ = 0, V = 0;
     try {
         pb.G = G;
         pack_operators(pb);
-        hp.resize(pb.pidx.n);
-        RBF_CUDA(cudaMemcpy(hp.data(), pb.pidx.p, pb.pidx.bytes(), cudaMemcpyDeviceToHost));
+        hp = to_host(pb.pidx);
+        hw = to_host(pb.pw);
+        SLQ = pb.SLQ;
+        V = pb.V;
     } catch (...) {
         restore();
         throw;
     }
-    ps.pw = std::move(pb.pw);
-    ps.G = G;
-    ps.SLQ = pb.SLQ;
-    ps.V = pb.V;
     restore();
+    const size_t ts = pb.tsize();
+    const int GV = G * V;                       // slots of one node per operand vector
 
-    // halo lists: own nodes first, then every other record the CTA's
-    // stencils read, ascending; slots refer to positions in the list
-    const int grid = div_up(pb.n_prog, chunk);
-    const int lanes = G * ps.V;            // slots of one node per operand vector
-    std::vector<int32_t> hoff(grid + 1, 0), hlist;
-    std::vector<uint16_t> lidx(hp.size());
-    std::vector<int32_t> other;
-    int halo_max = 0;
-    for (int c = 0; c < grid; ++c) {
-        const int64_t n0 = (int64_t)c * chunk, n1 = std::min<int64_t>(n0 + chunk, pb.n_prog);
-        other.clear();
-        for (int q = 0; q < ps.SLQ; ++q)
-            for (int64_t i = n0; i < n1; ++i)
-                for (int s = 0; s < lanes; ++s) {
-                    const int32_t j = hp[((int64_t)q * pb.n_prog + i) * lanes + s];
-                    if (j < n0 || j >= n1) other.push_back(j);
-                }
-        std::sort(other.begin(), other.end());
-        other.erase(std::unique(other.begin(), other.end()), other.end());
-        const int64_t nh = (n1 - n0) + (int64_t)other.size();
-        if (nh > 65535) return false;
-        halo_max = std::max<int>(halo_max, (int)nh);
-        hoff[c] = (int32_t)hlist.size();
-        for (int64_t i = n0; i < n1; ++i) hlist.push_back((int32_t)i);
-        hlist.insert(hlist.end(), other.begin(), other.end());
-        for (int q = 0; q < ps.SLQ; ++q)
-            for (int64_t i = n0; i < n1; ++i)
-                for (int s = 0; s < lanes; ++s) {
-                    const int64_t e = ((int64_t)q * pb.n_prog + i) * lanes + s;
-                    const int32_t j = hp[e];
-                    const int64_t loc =
-                        (j >= n0 && j < n1)
-                            ? j - n0
-                            : (n1 - n0) + (std::lower_bound(other.begin(), other.end(), j) - other.begin());
-                    lidx[e] = (uint16_t)loc;
-                }
+    // ---- blocks -----------------------------------------------------------------
+    std::vector<double> x(P), z(P);
+    RBF_CUDA(cudaMemcpy(x.data(), pb.x.p, P * 8, cudaMemcpyDeviceToHost));
+    RBF_CUDA(cudaMemcpy(z.data(), pb.z.p, P * 8, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> ids(P);
+    for (int64_t k = 0; k < P; ++k) ids[k] = (int32_t)k;
+    std::vector<std::pair<size_t, size_t>> blocks;
+    bisect(ids, 0, P, grid, x, z, blocks);
+    for (auto &b : blocks) {
+        if ((int)(b.second - b.first) > chunk || b.second == b.first) return false;
+        std::sort(ids.begin() + b.first, ids.begin() + b.second);
     }
-    hoff[grid] = (int32_t)hlist.size();
-    const size_t smem = (size_t)halo_max * 4 * pb.tsize();
-    if (smem > (size_t)smem_optin) return false;
 
-    // kernel variant: operands in registers when they fit, else read each stage
+    // ---- ghost systems: bands of the inverse rows ---------------------------------
+    const GhostPlan &gh = pb.gh;
+    const int64_t ng = gh.n_ghost > 0 ? gh.rows : 0;
+    const int npad = gh.npad;
+    std::vector<int32_t> gidx, owner, posv, comp_of;
+    std::vector<unsigned char> gwv, tbv, invv;
+    std::vector<int64_t> grec, cstart, ioff;
+    std::vector<int32_t> at;                                       // position -> row
+    std::vector<std::vector<std::pair<int32_t, double>>> band;     // [class * ng + position]
+    int cls_fields[4] = {0, 0, 0, 0};
+    if (ng > 0) {
+        gidx = to_host(gh.gidx);
+        gwv = to_host(gh.gw);
+        owner = to_host(gh.owner);
+        tbv = to_host(gh.tb);
+        posv = to_host(gh.pos);
+        grec = to_host(gh.grec);
+        comp_of = to_host(gh.comp_of);
+        cstart = to_host(gh.comp_start);
+        ioff = to_host(gh.inv_off);
+        invv = to_host(gh.inv);
+        for (int f = 0; f < 4; ++f) cls_fields[gh.field_class[f]] |= 1 << f;
+        at.resize(ng);
+        for (int64_t q = 0; q < ng; ++q) at[q] = (int32_t)(grec[q] - P);
+        const double thr = std::ldexp(pb.precision == 64 ? 2.220446049250313e-16 : 1.1920928955078125e-07, -8);
+        auto inv_at = [&](int64_t e) {
+            if (pb.precision == 64) {
+                double v;
+                memcpy(&v, invv.data() + e * 8, 8);
+                return v;
+            }
+            float v;
+            memcpy(&v, invv.data() + e * 4, 4);
+            return (double)v;
+        };
+        band.resize((size_t)gh.n_class * ng);
+        for (int cl = 0; cl < gh.n_class; ++cl)
+            for (int64_t q = 0; q < ng; ++q) {
+                const int c = comp_of[q];
+                const int64_t s0 = cstart[c];
+                const int m = (int)(cstart[c + 1] - s0);
+                const int64_t row0 = ioff[cl * gh.n_comp + c] + (q - s0) * m;
+                double mx = 0.0;
+                for (int j = 0; j < m; ++j) mx = std::max(mx, std::fabs(inv_at(row0 + j)));
+                auto &bd = band[(size_t)cl * ng + q];
+                for (int j = 0; j < m; ++j) {
+                    const double v = inv_at(row0 + j);
+                    if (v != 0.0 && std::fabs(v) >= thr * mx) bd.emplace_back((int32_t)(s0 + j), v);
+                }
+            }
+    }
+
+    // ---- per-CTA lists, operators and ghost blocks ----------------------------------
+    const int64_t lanes = (int64_t)grid * chunk;
+    std::vector<int32_t> hlist;
+    std::vector<CtaInfo> info(grid);
+    std::vector<unsigned char> blob;
+    std::vector<uint16_t> lidx((size_t)SLQ * lanes * GV, 0);
+    std::vector<unsigned char> pwp((size_t)4 * SLQ * lanes * GV * ts, 0);
+    const int64_t tot_old = (int64_t)SLQ * P * GV;
+    const int64_t tot_new = (int64_t)SLQ * lanes * GV;
+    std::vector<int32_t> stamp(pb.n_all, -1), loc(pb.n_all, 0);
+    std::vector<int32_t> rstamp(ng, -1), rloc(ng, 0);
+    int halo_max = 0, rows_max = 0;
+    size_t smem_max = 0;
+    std::vector<int32_t> other, ghosts, rows;
+    for (int c = 0; c < grid; ++c) {
+        const size_t b0 = blocks[c].first;
+        const int n_own = (int)(blocks[c].second - b0);
+        CtaInfo &ci = info[c];
+        memset(&ci, 0, sizeof(ci));
+        other.clear();
+        ghosts.clear();
+        rows.clear();
+        for (int li = 0; li < n_own; ++li) {
+            stamp[ids[b0 + li]] = c;
+            loc[ids[b0 + li]] = li;
+        }
+        auto add = [&](int32_t j) {
+            if (stamp[j] == c) return;
+            stamp[j] = c;
+            (j >= P ? ghosts : other).push_back(j);
+        };
+        for (int li = 0; li < n_own; ++li)
+            for (int q = 0; q < SLQ; ++q)
+                for (int s = 0; s < GV; ++s) add(hp[((int64_t)q * P + ids[b0 + li]) * GV + s]);
+        // wall rows in the bands of the ghosts it reads
+        for (int32_t gr : ghosts) {
+            const int64_t q = posv[gr - P];
+            for (int cl = 0; cl < gh.n_class; ++cl)
+                for (auto &e : band[(size_t)cl * ng + q])
+                    if (rstamp[e.first] != c) {
+                        rstamp[e.first] = c;
+                        rows.push_back(e.first);
+                    }
+        }
+        std::sort(rows.begin(), rows.end());
+        for (size_t k = 0; k < rows.size(); ++k) rloc[rows[k]] = (int32_t)k;
+        for (int32_t rp : rows) {
+            const int32_t r = at[rp];
+            for (int k = 0; k < npad; ++k) add(gidx[(int64_t)r * npad + k]);
+            add(owner[r]);
+        }
+        std::sort(other.begin(), other.end());
+        std::sort(ghosts.begin(), ghosts.end());
+        const int n_list = n_own + (int)other.size() + (int)ghosts.size();
+        if (n_list > 65535) return false;
+        ci.list_off = (int32_t)hlist.size();
+        ci.n_own = n_own;
+        ci.n_load = n_own + (int)other.size();
+        ci.n_list = n_list;
+        for (int li = 0; li < n_own; ++li) hlist.push_back(ids[b0 + li]);
+        for (size_t k = 0; k < other.size(); ++k) {
+            loc[other[k]] = n_own + (int32_t)k;
+            hlist.push_back(other[k]);
+        }
+        for (size_t k = 0; k < ghosts.size(); ++k) {
+            loc[ghosts[k]] = ci.n_load + (int32_t)k;
+            hlist.push_back(ghosts[k]);
+        }
+        halo_max = std::max(halo_max, n_list);
+
+        // lane operators in block order; idle lanes repeat the first node
+        for (int li = 0; li < chunk; ++li) {
+            const int64_t i = ids[b0 + (li < n_own ? li : 0)];
+            const int64_t p = (int64_t)c * chunk + li;
+            for (int q = 0; q < SLQ; ++q)
+                for (int s = 0; s < GV; ++s) {
+                    const int64_t eo = ((int64_t)q * P + i) * GV + s, en = ((int64_t)q * lanes + p) * GV + s;
+                    lidx[en] = (uint16_t)loc[hp[eo]];
+                    for (int f = 0; f < 4; ++f)
+                        memcpy(pwp.data() + ((size_t)f * tot_new + en) * ts,
+                               hw.data() + ((size_t)f * tot_old + eo) * ts, ts);
+                }
+        }
+
+        // ghost block: row slots, weight sets, row info, pairs, band coefficients
+        const int n_rows = (int)rows.size();
+        ci.n_rows = n_rows;
+        ci.blob_off = (int64_t)blob.size();
+        rows_max = std::max(rows_max, n_rows);
+        if (n_rows > 0) {
+            // distinct weight sets of each row (fields with the same boundary operator share one)
+            std::vector<std::vector<int>> setof(n_rows, std::vector<int>(4, 0));
+            std::vector<std::vector<int>> sets(n_rows);
+            int n_set = 1;
+            for (int k = 0; k < n_rows; ++k) {
+                const int32_t r = at[rows[k]];
+                for (int f = 0; f < 4; ++f) {
+                    const unsigned char *wf = gwv.data() + ((size_t)f * ng + r) * npad * ts;
+                    int found = -1;
+                    for (size_t s = 0; s < sets[k].size(); ++s) {
+                        const unsigned char *ws = gwv.data() + ((size_t)sets[k][s] * ng + r) * npad * ts;
+                        if (memcmp(wf, ws, npad * ts) == 0) found = (int)s;
+                    }
+                    if (found < 0) {
+                        found = (int)sets[k].size();
+                        sets[k].push_back(f);
+                    }
+                    setof[k][f] = found;
+                }
+                n_set = std::max(n_set, (int)sets[k].size());
+            }
+            ci.n_set = n_set;
+            std::vector<unsigned char> b;
+            std::vector<uint16_t> rs((size_t)n_rows * npad);
+            std::vector<int32_t> ri(n_rows);
+            for (int k = 0; k < n_rows; ++k) {
+                const int32_t r = at[rows[k]];
+                for (int t = 0; t < npad; ++t) rs[(size_t)k * npad + t] = (uint16_t)loc[gidx[(int64_t)r * npad + t]];
+                ri[k] = loc[owner[r]] | (tbv[r] ? 1 << 16 : 0) | (setof[k][0] << 17) | (setof[k][1] << 19) |
+                        (setof[k][2] << 21) | (setof[k][3] << 23);
+            }
+            put(b, 0, rs.data(), rs.size() * 2);
+            ci.o_rw = (int32_t)align16(b.size());
+            b.resize(ci.o_rw + (size_t)n_rows * n_set * npad * ts, 0);
+            for (int k = 0; k < n_rows; ++k) {
+                const int32_t r = at[rows[k]];
+                for (size_t s = 0; s < sets[k].size(); ++s)
+                    put(b, ci.o_rw + ((size_t)k * n_set + s) * npad * ts,
+                        gwv.data() + ((size_t)sets[k][s] * ng + r) * npad * ts, npad * ts);
+            }
+            ci.o_rinfo = (int32_t)align16(b.size());
+            put(b, ci.o_rinfo, ri.data(), ri.size() * 4);
+            // (ghost, class) pairs and their band coefficients
+            std::vector<int32_t> gcv;
+            std::vector<uint16_t> cix;
+            std::vector<unsigned char> cvl;
+            for (int32_t gr : ghosts) {
+                const int64_t q = posv[gr - P];
+                for (int cl = 0; cl < gh.n_class; ++cl) {
+                    if (!cls_fields[cl]) continue;
+                    const auto &bd = band[(size_t)cl * ng + q];
+                    gcv.push_back(loc[gr]);
+                    gcv.push_back(cls_fields[cl]);
+                    gcv.push_back((int32_t)cix.size());
+                    gcv.push_back((int32_t)bd.size());
+                    for (auto &e : bd) {
+                        cix.push_back((uint16_t)rloc[e.first]);
+                        if (pb.precision == 64) {
+                            const double v = e.second;
+                            cvl.insert(cvl.end(), (const unsigned char *)&v, (const unsigned char *)&v + 8);
+                        } else {
+                            const float v = (float)e.second;   // exact: the inverse is stored in FP32
+                            cvl.insert(cvl.end(), (const unsigned char *)&v, (const unsigned char *)&v + 4);
+                        }
+                    }
+                }
+            }
+            ci.n_gc = (int32_t)(gcv.size() / 4);
+            ci.n_coef = (int32_t)cix.size();
+            ci.o_gc = (int32_t)align16(b.size());
+            put(b, ci.o_gc, gcv.data(), gcv.size() * 4);
+            ci.o_cidx = (int32_t)align16(b.size());
+            put(b, ci.o_cidx, cix.data(), cix.size() * 2);
+            ci.o_cval = (int32_t)align16(b.size());
+            put(b, ci.o_cval, cvl.data(), cvl.size());
+            b.resize(align16(b.size()), 0);
+            ci.blob_bytes = (int32_t)b.size();
+            blob.insert(blob.end(), b.begin(), b.end());
+        }
+        const size_t sm = align16((size_t)n_list * 4 * ts) + align16((size_t)n_rows * 4 * ts) + ci.blob_bytes;
+        smem_max = std::max(smem_max, sm);
+    }
+    if (smem_max > (size_t)smem_optin) return false;
+
+    // ---- kernel variant: operators in registers when they fit ----------------------
     const std::vector<Variant> vs = pb.precision == 64 ? variants<double>() : variants<float>();
     int pick = -1;
     for (int k = 0; k < (int)vs.size(); ++k) {
         const Variant &v = vs[k];
         if (v.G != G || threads > v.maxt) continue;
-        if (v.R > 0 && ps.SLQ > v.R) continue;
+        if (v.R > 0 && SLQ > v.R) continue;
         if (pick < 0 || (v.R > 0 && vs[pick].R == 0)) pick = k;
     }
     if (pick < 0) return false;
-    RBF_CUDA(cudaFuncSetAttribute(vs[pick].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    RBF_CUDA(cudaFuncSetAttribute(vs[pick].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
     int per_sm = 0;
-    RBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vs[pick].fn, threads, smem));
+    RBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vs[pick].fn, threads, smem_max));
     if ((int64_t)per_sm * nsm < grid) return false;
 
+    ps.G = G;
+    ps.SLQ = SLQ;
+    ps.V = V;
     ps.R = vs[pick].R;
     ps.maxt = vs[pick].maxt;
     ps.chunk = chunk;
     ps.threads = threads;
     ps.grid = grid;
     ps.halo_max = halo_max;
-    ps.halo_total = (int64_t)hlist.size();
-    ps.smem = smem;
-    ps.hoff.alloc(hoff.size());
-    ps.hlist.alloc(hlist.size());
+    ps.rows_max = rows_max;
+    ps.smem = smem_max;
+    ps.pw.alloc(pwp.size());
     ps.lidx.alloc(lidx.size());
-    RBF_CUDA(cudaMemcpy(ps.hoff.p, hoff.data(), ps.hoff.bytes(), cudaMemcpyHostToDevice));
-    RBF_CUDA(cudaMemcpy(ps.hlist.p, hlist.data(), ps.hlist.bytes(), cudaMemcpyHostToDevice));
+    ps.hlist.alloc(hlist.size());
+    ps.cta.alloc(info.size() * sizeof(CtaInfo));
+    ps.blob.alloc(std::max<size_t>(blob.size(), 16));
+    RBF_CUDA(cudaMemcpy(ps.pw.p, pwp.data(), pwp.size(), cudaMemcpyHostToDevice));
     RBF_CUDA(cudaMemcpy(ps.lidx.p, lidx.data(), ps.lidx.bytes(), cudaMemcpyHostToDevice));
-    RBF_CUDA(cudaStreamSynchronize(pb.st));
+    RBF_CUDA(cudaMemcpy(ps.hlist.p, hlist.data(), ps.hlist.bytes(), cudaMemcpyHostToDevice));
+    RBF_CUDA(cudaMemcpy(ps.cta.p, info.data(), ps.cta.bytes(), cudaMemcpyHostToDevice));
+    if (!blob.empty()) RBF_CUDA(cudaMemcpy(ps.blob.p, blob.data(), blob.size(), cudaMemcpyHostToDevice));
     if (ps.arrive.n == 0) ps.arrive.alloc(1);
     RBF_CUDA(cudaMemset(ps.arrive.p, 0, sizeof(unsigned)));
     ps.base = 0;
@@ -597,9 +863,8 @@ void persistent_run(Problem &pb, double dt, int64_t n_steps, void *U, cudaStream
         void *args[] = {&a};
         RBF_CUDA(cudaLaunchCooperativeKernel(fn, dim3(ps.grid), dim3(ps.threads), args, ps.smem, s));
     }
-    // barriers of this launch: 3 per stage with ghosts, 1 without, minus the last
-    const int64_t per_stage = pb.gh.n_ghost > 0 && pb.gh.rows > 0 ? 3 : 1;
-    ps.base += (unsigned)((uint64_t)ps.grid * (uint64_t)(4 * per_stage * n_steps - 1));
+    // one barrier after every stage but the last
+    ps.base += (unsigned)((uint64_t)ps.grid * (uint64_t)(4 * n_steps - 1));
 }
 
 void persistent_check(Problem &pb) {

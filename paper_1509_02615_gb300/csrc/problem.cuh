@@ -50,24 +50,26 @@ struct GhostPlan {
 };
 
 // Persistent run mode: one cooperative launch runs all the steps of an
-// rbf_run (csrc/persistent.cu).  Its operators are packed for its own lane
-// count; each CTA's stencil records are listed once (its halo) and the
-// packed slots refer to positions in that list.
+// rbf_run (csrc/persistent.cu).  The nodes are split into compact blocks,
+// one per CTA; each block's list of the records its stencils read (own
+// nodes first), its lane operators packed in block order, and the constant
+// data of the ghost rows and ghost values it solves for itself.
 struct PersistPlan {
     bool ready = false;
     int G = 0;                   // lanes per node
     int R = 0;                   // operand vectors held in registers (0: read each stage)
     int maxt = 0;                // thread limit of the kernel variant
     int SLQ = 0, V = 0;          // packing of pw / lidx (as Problem::SLQ, V)
-    int chunk = 0;               // nodes per CTA
+    int chunk = 0;               // largest block (nodes per CTA)
     int threads = 0, grid = 0;
-    int halo_max = 0;
-    int64_t halo_total = 0;
+    int halo_max = 0;            // largest record list
+    int rows_max = 0;            // most ghost rows one CTA solves
     size_t smem = 0;
-    DevBuf<unsigned char> pw;    // T [4][SLQ][n_prog][G][V]
-    DevBuf<uint16_t> lidx;       // [SLQ][n_prog][G][V] halo position of each slot
-    DevBuf<int32_t> hoff;        // [grid + 1]
-    DevBuf<int32_t> hlist;       // halo records of each CTA: its own nodes first
+    DevBuf<unsigned char> pw;    // T [4][SLQ][grid * chunk][G][V]
+    DevBuf<uint16_t> lidx;       // [SLQ][grid * chunk][G][V] list position of each slot
+    DevBuf<int32_t> hlist;       // record lists of all CTAs
+    DevBuf<unsigned char> cta;   // per-CTA layout records
+    DevBuf<unsigned char> blob;  // per-CTA ghost-row and ghost-value data
     DevBuf<unsigned int> arrive; // barrier arrivals, monotone across launches
     unsigned base = 0;           // its value when the next launch starts
     DevBuf<int> abort;           // set when a barrier wait gives up (sticky until rbf_sync)

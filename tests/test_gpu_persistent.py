@@ -1,12 +1,14 @@
 """Persistent run mode: one cooperative launch runs every RK4 step of an
-rbf_run (ghost residuals, ghost solves and fused stages separated by grid
-barriers).  Checked against the graph mode (same lanes per node: the same
-operations in the same order, so bit-identical results), against the FP64
-oracle, and on its bounded-wait failure path.
+rbf_run; compact node blocks per CTA, ghosts solved inside each CTA from the
+banded inverse rows, one grid barrier per stage.  Checked against the FP64
+oracle, against the graph mode, and on its bounded-wait failure path.
 
-Tolerances: bitwise equality with the graph mode; FP64 against the oracle
-1e-11 relative l2 per field after the stated steps (the per-stage RHS
-parity bound of the graph mode, which these runs reproduce bit for bit).
+Tolerances (relative l2 per field over the prognostic nodes):
+  * FP64 against the oracle: 1e-12 after the stated steps;
+  * FP64 against the graph mode: 1e-13 (the two differ only in the order of
+    the ghost sums and in inverse entries below 2^-8 eps of their row);
+  * FP32 against the graph mode: 1e-5 after the stated steps (the same
+    differences at eps32 = 6e-8, grown over the run).
 """
 import numpy as np
 import pytest
@@ -44,49 +46,75 @@ def _both_modes(nodes, prec, G, dt, steps):
     assert info["run_mode"] == 2 and info["persist_lanes"] == G
     pb.run(0.0, dt, steps, B)
     pb.sync()
-    return pb, A, B, info
+    P = nodes.n_prog
+    a, b = rbffd.fields(A)[:, :P], rbffd.fields(B)[:, :P]
+    return pb, [rel(b[f], a[f]) for f in range(4)], info
+
+
+TOL = {64: 1e-13, 32: 1e-5}
 
 
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("G", [1, 2, 4])
-def test_persistent_equals_graph_bitwise_400m(prec, G):
+def test_persistent_matches_graph_400m(prec, G):
     nodes = inp.density_current_nodes(400.0)
-    pb, A, B, info = _both_modes(nodes, prec, G, 1.0, 25)
-    print(f"FP{prec} G={G}: chunk {info['persist_chunk']}, halo {info['persist_halo_max']}, "
-          f"registers {info['persist_regs']}")
-    assert torch.equal(A, B)
+    pb, errs, info = _both_modes(nodes, prec, G, 1.0, 25)
+    print(f"FP{prec} G={G}: chunk {info['persist_chunk']}, list {info['persist_halo_max']}, "
+          f"registers {info['persist_regs']}, vs graph {['%.1e' % e for e in errs]}")
+    assert max(errs) < TOL[prec], errs
     pb.close()
 
 
 @pytest.mark.parametrize("prec", [32, 64])
-def test_persistent_equals_graph_bitwise_100m(prec):
-    """The 100 m hexagonal density current (38,400 nodes, 253 per CTA):
+def test_persistent_matches_graph_100m(prec):
+    """The 100 m hexagonal density current (38,400 nodes, ~253 per CTA):
     the launch configuration the measurements use."""
     nodes = inp.density_current_nodes(100.0)
-    pb, A, B, info = _both_modes(nodes, prec, 1, 0.25, 40)
-    print(f"100 m FP{prec}: chunk {info['persist_chunk']}, halo {info['persist_halo_max']}, "
-          f"registers {info['persist_regs']}")
+    pb, errs, info = _both_modes(nodes, prec, 1, 0.25, 40)
+    print(f"100 m FP{prec}: chunk {info['persist_chunk']}, list {info['persist_halo_max']}, "
+          f"registers {info['persist_regs']}, vs graph {['%.1e' % e for e in errs]}")
     if prec == 32:
         assert info["persist_regs"] == 1
-    assert torch.equal(A, B)
+    assert max(errs) < TOL[prec], errs
     pb.close()
 
 
-def test_persistent_fp64_matches_oracle():
+@pytest.mark.parametrize("G", [1, 2, 4])
+def test_persistent_fp64_matches_oracle(G):
     nodes = inp.density_current_nodes(400.0)
     o = NSOracle(nodes)
     U0 = inp.density_current_state(nodes)
     ref = o.run(U0, 0.0, 1.0, 40)
-    pb = rbffd.ns_problem(nodes, precision=64, threads_per_node=2)
-    pb.set_run_mode("persistent")
+    pb = rbffd.ns_problem(nodes, precision=64, threads_per_node=G)
+    pb.set_run_mode("persistent", lanes=G)
     U = rbffd.state_tensor(U0, 64)
     pb.run(0.0, 1.0, 40, U)
     pb.sync()
     got = rbffd.fields(U)
     P = nodes.n_prog
     errs = [rel(got[f, :P], ref[f, :P]) for f in range(4)]
-    print("persistent FP64 vs oracle, 40 steps:", [f"{e:.2e}" for e in errs])
-    assert max(errs) < 1e-11
+    print(f"persistent FP64 G={G} vs oracle, 40 steps:", [f"{e:.2e}" for e in errs])
+    assert max(errs) < 1e-12
+
+
+def test_persistent_walled_bubble_fp64_matches_oracle():
+    """Lateral walls and corners: the warm bubble at 500 m (scattered nodes,
+    n = 56, r^9 + deg 5), whose ghost systems have several components and
+    classes."""
+    from paper_1509_02615_gb300 import configs
+    wl = configs.bubble(h=500.0, seed=1, t_end=30.0)
+    o = NSOracle(wl.nodes, **wl.params)
+    ref = o.run(wl.U0, 0.0, wl.dt, wl.n_steps)
+    pb = rbffd.ns_problem(wl.nodes, precision=64, threads_per_node=2, **wl.params)
+    pb.set_run_mode("persistent", lanes=2)
+    U = rbffd.state_tensor(wl.U0, 64)
+    pb.run(0.0, wl.dt, wl.n_steps, U)
+    pb.sync()
+    got = rbffd.fields(U)
+    P = wl.nodes.n_prog
+    errs = [rel(got[f, :P], ref[f, :P]) for f in (1, 2, 3)]   # u stays at rounding level
+    print("persistent FP64 bubble vs oracle:", [f"{e:.2e}" for e in errs])
+    assert max(errs) < 1e-10
 
 
 def test_persistent_timeout_reports_and_recovers():
@@ -112,7 +140,9 @@ def test_persistent_timeout_reports_and_recovers():
     pb.set_run_mode("graph")
     pb.run(0.0, 1.0, 5, V)
     pb.sync()
-    assert torch.equal(U, V)
+    P = nodes.n_prog
+    a, b = rbffd.fields(U)[:, :P], rbffd.fields(V)[:, :P]
+    assert max(rel(a[f], b[f]) for f in range(4)) < 1e-5
 
 
 def test_run_mode_arguments():
