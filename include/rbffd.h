@@ -326,13 +326,15 @@ int rbf_run(rbf_problem *pb, double t0, double dt, int64_t n_steps, void *U);
  *   RBF_RUN_AUTO        time both on a zero state and keep the faster
  *                       (done at creation when threads_per_node is 0).
  * lanes: lanes per node of the persistent kernel (1, 2 or 4; 0 = fastest).
+ * ctas:  CTAs of the persistent kernel (0: fastest of 1, 1/2, 1/4, 1/8 per
+ *        SM; with lanes > 0 and RBF_RUN_PERSISTENT, one per SM untimed).
  * Errors: RBF_E_ARG if the mode is unknown, the problem is not a
  * Navier-Stokes problem, or RBF_RUN_PERSISTENT does not fit.
  */
 #define RBF_RUN_AUTO 0
 #define RBF_RUN_GRAPH 1
 #define RBF_RUN_PERSISTENT 2
-int rbf_set_run_mode(rbf_problem *pb, int32_t mode, int32_t lanes);
+int rbf_set_run_mode(rbf_problem *pb, int32_t mode, int32_t lanes, int32_t ctas);
 
 /*
  * Bound on the polls of each grid-barrier wait of the persistent kernel
@@ -381,6 +383,8 @@ typedef struct rbf_info {
     int32_t persist_regs;       /* 1: it keeps its operands in registers    */
     int32_t persist_chunk;      /* nodes per CTA                            */
     int32_t persist_halo_max;   /* largest per-CTA record list              */
+    int32_t persist_ctas;       /* CTAs of the persistent launch            */
+    int32_t reserved2;
 } rbf_info;
 int rbf_get_info(const rbf_problem *pb, rbf_info *out);
 

@@ -188,46 +188,70 @@ float time_run(Problem &pb, void *U, int steps) {
 }
 
 // Run-mode autotuner: graph replay against the persistent kernel for each
-// lane count that fits, on a zero state; keeps the fastest.  lanes > 0
-// restricts the persistent candidates to that lane count.
-void choose_run_mode(Problem &pb, int mode, int lanes) {
+// (lanes per node, CTA count) that fits, on a zero state; keeps the fastest.
+// lanes > 0 restricts the persistent candidates to that lane count, ctas > 0
+// to that CTA count; with both given (RBF_RUN_PERSISTENT) nothing is timed.
+void choose_run_mode(Problem &pb, int mode, int lanes, int ctas) {
     RBF_REQUIRE(pb.kind == kNS, "run modes apply to Navier-Stokes problems");
     RBF_REQUIRE(mode == RBF_RUN_AUTO || mode == RBF_RUN_GRAPH || mode == RBF_RUN_PERSISTENT,
                 "unknown run mode %d", mode);
     RBF_REQUIRE(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4, "lanes must be 0, 1, 2 or 4");
+    RBF_REQUIRE(ctas >= 0, "ctas must be >= 0");
     if (mode == RBF_RUN_GRAPH) {
         pb.run_mode = RBF_RUN_GRAPH;
         return;
     }
-    std::vector<int> cands;
-    if (lanes) cands.push_back(lanes);
-    else cands = {1, 2, 4};
+    const int nsm = sm_count();
+    std::vector<std::pair<int, int>> cands;
+    for (int G : {1, 2, 4}) {
+        if (lanes && G != lanes) continue;
+        if (ctas) {
+            cands.emplace_back(G, ctas);
+            continue;
+        }
+        // explicit lanes without a CTA count: one CTA per SM, untimed
+        if (lanes && mode == RBF_RUN_PERSISTENT) {
+            cands.emplace_back(G, nsm);
+            continue;
+        }
+        for (int div : {1, 2, 4, 8}) {
+            const int c = nsm / div;
+            if (c >= 1 && (div == 1 || (int64_t)c * 8 <= pb.n_prog)) cands.emplace_back(G, c);
+        }
+    }
     const bool timing = mode == RBF_RUN_AUTO || cands.size() > 1;
     const size_t bytes = (size_t)pb.F * pb.n_all * pb.tsize();
     DevBuf<unsigned char> U(timing ? bytes : 0);
     if (timing) RBF_CUDA(cudaMemsetAsync(U.p, 0, bytes, pb.st));
     const int steps = 8;
     float best = 1e30f;
-    int bestG = 0;
+    std::pair<int, int> pick(0, 0);
     if (mode == RBF_RUN_AUTO) {
         pb.run_mode = RBF_RUN_GRAPH;
         best = time_run(pb, U.p, steps);
         invalidate_graph(pb);
     }
-    for (int G : cands) {
-        if (!persistent_plan(pb, G)) continue;
-        if (!timing) { bestG = G; break; }
+    for (auto &c : cands) {
+        if (!persistent_plan(pb, c.first, c.second)) continue;
+        if (!timing) {
+            pick = c;
+            break;
+        }
         pb.run_mode = RBF_RUN_PERSISTENT;
         const float t = time_run(pb, U.p, steps);
-        if (t < best) { best = t; bestG = G; }
+        if (t < best) {
+            best = t;
+            pick = c;
+        }
     }
-    if (bestG == 0) {
+    if (pick.first == 0) {
         pb.ps.ready = false;
         pb.run_mode = RBF_RUN_GRAPH;
         RBF_REQUIRE(mode == RBF_RUN_AUTO, "the persistent kernel does not fit this problem");
         return;
     }
-    if (!pb.ps.ready || pb.ps.G != bestG) persistent_plan(pb, bestG);
+    if (!pb.ps.ready || pb.ps.G != pick.first || pb.ps.grid != std::min<int64_t>(pick.second, pb.n_prog))
+        persistent_plan(pb, pick.first, pick.second);
     RBF_REQUIRE(pb.ps.ready, "persistent plan failed");
     pb.run_mode = RBF_RUN_PERSISTENT;
     // zero the stage buffers the timing runs wrote (ghost records included)
@@ -313,7 +337,7 @@ void build_ns(Problem &pb, const rbf_ns_params &prm, const double *x, const doub
     rbf::build_ghost_plan(pb, kind, ghost_owner);
     if (with_scratch) rbf::alloc_scratch(pb);
     rbf::choose_threads(pb, prm.threads_per_node);
-    if (with_scratch && prm.threads_per_node == 0) rbf::choose_run_mode(pb, RBF_RUN_AUTO, 0);
+    if (with_scratch && prm.threads_per_node == 0) rbf::choose_run_mode(pb, RBF_RUN_AUTO, 0, 0);
     RBF_CUDA(cudaStreamSynchronize(pb.st));
 }
 
@@ -455,13 +479,13 @@ int rbf_sync(rbf_problem *h) {
     });
 }
 
-int rbf_set_run_mode(rbf_problem *h, int32_t mode, int32_t lanes) {
+int rbf_set_run_mode(rbf_problem *h, int32_t mode, int32_t lanes, int32_t ctas) {
     return rbf::guarded([&] {
         RBF_REQUIRE(h, "null problem");
         Problem &pb = h->impl;
         RBF_CUDA(cudaStreamSynchronize(pb.st));
         RBF_CUDA(cudaStreamSynchronize(pb.cap));
-        rbf::choose_run_mode(pb, mode, lanes);
+        rbf::choose_run_mode(pb, mode, lanes, ctas);
     });
 }
 
@@ -504,6 +528,7 @@ int rbf_get_info(const rbf_problem *h, rbf_info *out) {
             out->persist_regs = pb.ps.R > 0 ? 1 : 0;
             out->persist_chunk = pb.ps.chunk;
             out->persist_halo_max = pb.ps.halo_max;
+            out->persist_ctas = pb.ps.grid;
         }
         out->weight_build_ms = pb.weight_build_ms;
         out->ghost_setup_ms = pb.ghost_setup_ms;

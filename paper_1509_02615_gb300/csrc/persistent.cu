@@ -18,7 +18,8 @@
 // the dropped part is below the rounding of the kept sum.  A CTA whose
 // stencils read ghosts forms, from its shared-memory records, the residuals
 // of every wall row in those ghosts' bands, then the ghost values it needs
-// (4 lanes per ghost and operator class, every field of the class at once).
+// (every field of an operator class at once; the lanes per row and per
+// ghost are chosen so that one pass of the CTA's threads covers them).
 //
 // One stage per CTA: copy the listed records of the stage input into
 // shared memory (its own nodes' from registers, the others in one round of
@@ -151,6 +152,8 @@ struct CtaInfo {
     int32_t n_gc;       // (ghost, operator class) pairs it solves
     int32_t n_set;      // weight sets per wall row
     int32_t n_coef;     // band coefficients of all its pairs
+    int32_t row_pad;    // row stride of the slot-major row arrays (bank-conflict free)
+    int32_t pad_;
     int64_t blob_off;   // byte offset of its constant block
     int32_t blob_bytes;
     int32_t o_rw, o_rinfo, o_gc, o_cidx, o_cval;   // sections of the block (row slots at 0)
@@ -180,8 +183,16 @@ struct PArgs {
     long long spin_limit;
 };
 
-constexpr int kRowLanes = 8;    // lanes per wall row in the residuals, as the ghost kernels
-constexpr int kPairLanes = 4;   // lanes per (ghost, class) pair in the ghost values
+constexpr int kRowLanes = 8;    // most lanes per wall row in the residuals
+constexpr int kPairLanes = 8;   // most lanes per (ghost, class) pair in the ghost values
+
+// Lanes per item: the largest power of two up to `most` with items * lanes
+// within one pass of the CTA's threads (at least one lane).
+__host__ __device__ __forceinline__ int lanes_for(int items, int threads, int most) {
+    int l = most;
+    while (l > 1 && items * l > threads) l >>= 1;
+    return l;
+}
 
 template <class T, int G, int R, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant__ PArgs<T> a) {
@@ -261,59 +272,68 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
             __syncthreads();
             if (ci.n_rows > 0) {
                 // ---- residuals b - W_I u_I - W_B u_B of its wall rows -----------
-                // 8 lanes per row (unrolled so that a lane's loads overlap)
-                const int per = a.npad / kRowLanes;
-                const int nlr = (ci.n_rows * kRowLanes + 31) & ~31;
+                // L lanes per row, L the largest of 8, 4, 2, 1 that lets one pass
+                // of the CTA's threads cover every row
+                const int L = lanes_for(ci.n_rows, blockDim.x, kRowLanes);
+                const int per = a.npad / L;
+                const int nlr = (ci.n_rows * L + 31) & ~31;
                 for (int e = threadIdx.x; e < nlr; e += blockDim.x) {
-                    int r = e / kRowLanes;
-                    const int ln = e % kRowLanes;
+                    int r = e / L;
+                    const int ln = e % L;
                     const bool rl = r < ci.n_rows;
                     if (!rl) r = ci.n_rows - 1;
                     const int inf = rinfo[r];
-                    const T *w0 = rw + ((size_t)r * ci.n_set + ((inf >> 17) & 3)) * a.npad + ln;
-                    const T *w1 = rw + ((size_t)r * ci.n_set + ((inf >> 19) & 3)) * a.npad + ln;
-                    const T *w2 = rw + ((size_t)r * ci.n_set + ((inf >> 21) & 3)) * a.npad + ln;
-                    const T *w3 = rw + ((size_t)r * ci.n_set + ((inf >> 23) & 3)) * a.npad + ln;
-                    const uint16_t *rj = ridx + (size_t)r * a.npad + ln;
+                    // slot-major [set][slot][row_pad]: the lanes of a warp read
+                    // consecutive rows of one slot
+                    const size_t RP = ci.row_pad, step = (size_t)L * RP;
+                    const T *w0 = rw + ((size_t)((inf >> 17) & 3) * a.npad + ln) * RP + r;
+                    const T *w1 = rw + ((size_t)((inf >> 19) & 3) * a.npad + ln) * RP + r;
+                    const T *w2 = rw + ((size_t)((inf >> 21) & 3) * a.npad + ln) * RP + r;
+                    const T *w3 = rw + ((size_t)((inf >> 23) & 3) * a.npad + ln) * RP + r;
+                    const uint16_t *rj = ridx + (size_t)ln * RP + r;
                     T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
 #pragma unroll 4
                     for (int t = 0; t < per; ++t) {
-                        const Rec<T> v = sh_rec(halo, rj[kRowLanes * t]);
-                        a0 += w0[kRowLanes * t] * v.u;
-                        a1 += w1[kRowLanes * t] * v.w;
-                        a2 += w2[kRowLanes * t] * v.t;
-                        a3 += w3[kRowLanes * t] * v.p;
+                        const Rec<T> v = sh_rec(halo, rj[t * step]);
+                        a0 += w0[t * step] * v.u;
+                        a1 += w1[t * step] * v.w;
+                        a2 += w2[t * step] * v.t;
+                        a3 += w3[t * step] * v.p;
                     }
+                    for (int o = L / 2; o > 0; o >>= 1) {
+                        a0 += __shfl_xor_sync(0xffffffffu, a0, o, L);
+                        a1 += __shfl_xor_sync(0xffffffffu, a1, o, L);
+                        a2 += __shfl_xor_sync(0xffffffffu, a2, o, L);
+                        a3 += __shfl_xor_sync(0xffffffffu, a3, o, L);
+                    }
+                    if (rl) {
 #pragma unroll
-                    for (int o = kRowLanes / 2; o > 0; o >>= 1) {
-                        a0 += __shfl_xor_sync(0xffffffffu, a0, o, kRowLanes);
-                        a1 += __shfl_xor_sync(0xffffffffu, a1, o, kRowLanes);
-                        a2 += __shfl_xor_sync(0xffffffffu, a2, o, kRowLanes);
-                        a3 += __shfl_xor_sync(0xffffffffu, a3, o, kRowLanes);
-                    }
-                    if (rl && ln < 4) {
-                        const T acc = ln == 0 ? a0 : ln == 1 ? a1 : ln == 2 ? a2 : a3;
-                        T b = 0;
-                        if (ln == 3 && (inf & (1 << 16))) {
-                            // pi'_z = g theta' / (c_p theta_bar (theta_bar + theta')) at the wall node
-                            const T th = halo[(size_t)(inf & 0xffff) * 4 + 2];
-                            b = a.gconst * th / (a.cp_tb2 + a.cp_tb2 / a.theta_bar * th);
+                        for (int f = 0; f < 4; ++f) {
+                            if (f % L != ln) continue;
+                            const T acc = f == 0 ? a0 : f == 1 ? a1 : f == 2 ? a2 : a3;
+                            T b = 0;
+                            if (f == 3 && (inf & (1 << 16))) {
+                                // pi'_z = g theta' / (c_p theta_bar (theta_bar + theta')) at the wall node
+                                const T th = halo[(size_t)(inf & 0xffff) * 4 + 2];
+                                b = a.gconst * th / (a.cp_tb2 + a.cp_tb2 / a.theta_bar * th);
+                            }
+                            res[f * ci.n_rows + r] = b - acc;
                         }
-                        res[ln * ci.n_rows + r] = b - acc;
                     }
                 }
                 __syncthreads();
                 // ---- ghost values from the banded inverse rows -------------------
-                // 4 lanes per (ghost, class) pair, every field of the class at once
-                const int npl = (ci.n_gc * kPairLanes + 31) & ~31;
+                // M lanes per (ghost, class) pair, every field of the class at once
+                const int M = lanes_for(ci.n_gc, blockDim.x, kPairLanes);
+                const int npl = (ci.n_gc * M + 31) & ~31;
                 for (int e = threadIdx.x; e < npl; e += blockDim.x) {
-                    const int k = e / kPairLanes, ln = e % kPairLanes;
+                    const int k = e / M, ln = e % M;
                     const int4 gc = gcs[k < ci.n_gc ? k : ci.n_gc - 1];   // position, field mask, first, count
                     T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
                     const uint16_t *cj = cidx + gc.z;
                     const T *cv = cval + gc.z;
 #pragma unroll 4
-                    for (int j = ln; j < gc.w; j += kPairLanes) {
+                    for (int j = ln; j < gc.w; j += M) {
                         const T c = cv[j];
                         const int rr = cj[j];
                         if (gc.y & 1) s0 += c * res[rr];
@@ -321,15 +341,18 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
                         if (gc.y & 4) s2 += c * res[2 * ci.n_rows + rr];
                         if (gc.y & 8) s3 += c * res[3 * ci.n_rows + rr];
                     }
-#pragma unroll
-                    for (int o = kPairLanes / 2; o > 0; o >>= 1) {
-                        s0 += __shfl_xor_sync(0xffffffffu, s0, o, kPairLanes);
-                        s1 += __shfl_xor_sync(0xffffffffu, s1, o, kPairLanes);
-                        s2 += __shfl_xor_sync(0xffffffffu, s2, o, kPairLanes);
-                        s3 += __shfl_xor_sync(0xffffffffu, s3, o, kPairLanes);
+                    for (int o = M / 2; o > 0; o >>= 1) {
+                        s0 += __shfl_xor_sync(0xffffffffu, s0, o, M);
+                        s1 += __shfl_xor_sync(0xffffffffu, s1, o, M);
+                        s2 += __shfl_xor_sync(0xffffffffu, s2, o, M);
+                        s3 += __shfl_xor_sync(0xffffffffu, s3, o, M);
                     }
-                    if (k < ci.n_gc && ln < 4 && (gc.y & (1 << ln)))
-                        halo[(size_t)gc.x * 4 + ln] = ln == 0 ? s0 : ln == 1 ? s1 : ln == 2 ? s2 : s3;
+                    if (k < ci.n_gc) {
+#pragma unroll
+                        for (int f = 0; f < 4; ++f)
+                            if (f % M == ln && (gc.y & (1 << f)))
+                                halo[(size_t)gc.x * 4 + f] = f == 0 ? s0 : f == 1 ? s1 : f == 2 ? s2 : s3;
+                    }
                 }
                 __syncthreads();
             }
@@ -518,7 +541,7 @@ void put(std::vector<unsigned char> &b, size_t at, const void *src, size_t bytes
 
 }  // namespace
 
-bool persistent_plan(Problem &pb, int G) {
+bool persistent_plan(Problem &pb, int G, int ctas) {
     PersistPlan &ps = pb.ps;
     ps.ready = false;
     if (pb.kind != kNS) return false;
@@ -529,7 +552,7 @@ bool persistent_plan(Problem &pb, int G) {
     if (!coop) return false;
     const int nsm = sm_count();
     const int64_t P = pb.n_prog;
-    const int grid = (int)std::min<int64_t>(nsm, P);
+    const int grid = (int)std::min<int64_t>(ctas > 0 ? ctas : nsm, P);
     const int chunk = div_up(P, grid) + 1;   // bisection blocks differ by at most one node
     const int threads = div_up((int64_t)chunk * G, 32) * 32;
     if (threads > 1024) return false;
@@ -739,23 +762,30 @@ bool persistent_plan(Problem &pb, int G) {
                 n_set = std::max(n_set, (int)sets[k].size());
             }
             ci.n_set = n_set;
+            // row stride: the L lane groups of a warp (32 / L consecutive rows
+            // each) start 32 / L banks apart
+            const int L = lanes_for(n_rows, threads, kRowLanes);
+            int RP = n_rows;
+            while (RP % 32 != (32 / L) % 32) ++RP;
+            ci.row_pad = RP;
             std::vector<unsigned char> b;
-            std::vector<uint16_t> rs((size_t)n_rows * npad);
+            std::vector<uint16_t> rs((size_t)npad * RP, 0);
             std::vector<int32_t> ri(n_rows);
             for (int k = 0; k < n_rows; ++k) {
                 const int32_t r = at[rows[k]];
-                for (int t = 0; t < npad; ++t) rs[(size_t)k * npad + t] = (uint16_t)loc[gidx[(int64_t)r * npad + t]];
+                for (int t = 0; t < npad; ++t) rs[(size_t)t * RP + k] = (uint16_t)loc[gidx[(int64_t)r * npad + t]];
                 ri[k] = loc[owner[r]] | (tbv[r] ? 1 << 16 : 0) | (setof[k][0] << 17) | (setof[k][1] << 19) |
                         (setof[k][2] << 21) | (setof[k][3] << 23);
             }
             put(b, 0, rs.data(), rs.size() * 2);
             ci.o_rw = (int32_t)align16(b.size());
-            b.resize(ci.o_rw + (size_t)n_rows * n_set * npad * ts, 0);
+            b.resize(ci.o_rw + (size_t)n_set * npad * RP * ts, 0);
             for (int k = 0; k < n_rows; ++k) {
                 const int32_t r = at[rows[k]];
                 for (size_t s = 0; s < sets[k].size(); ++s)
-                    put(b, ci.o_rw + ((size_t)k * n_set + s) * npad * ts,
-                        gwv.data() + ((size_t)sets[k][s] * ng + r) * npad * ts, npad * ts);
+                    for (int t = 0; t < npad; ++t)
+                        put(b, ci.o_rw + (((size_t)s * npad + t) * RP + k) * ts,
+                            gwv.data() + (((size_t)sets[k][s] * ng + r) * npad + t) * ts, ts);
             }
             ci.o_rinfo = (int32_t)align16(b.size());
             put(b, ci.o_rinfo, ri.data(), ri.size() * 4);

@@ -155,9 +155,10 @@ void build_ensemble(Problem &pb, const rbf_ns_params &common, int n, const rbf_e
                     const double *z, const int32_t *kind, const int32_t *owner, void *stream);
 void run_ensemble(Problem &pb, int64_t max_steps, void *U);
 double ensemble_node_updates(const Problem &pb, int64_t max_steps);
-// Builds the persistent plan for G lanes per node; false if the problem does
-// not fit one co-resident launch (pb.ps.ready tells the same).
-bool persistent_plan(Problem &pb, int G);
+// Builds the persistent plan for G lanes per node on `ctas` CTAs (0: one per
+// SM); false if the problem does not fit one co-resident launch (pb.ps.ready
+// tells the same).
+bool persistent_plan(Problem &pb, int G, int ctas);
 void persistent_run(Problem &pb, double dt, int64_t n_steps, void *U, cudaStream_t s);
 // RBF_E_TIMEOUT (and clears the flag) if a persistent launch gave up a wait.
 void persistent_check(Problem &pb);

@@ -54,7 +54,7 @@ class Info(C.Structure):
                 ("weight_build_ms", C.c_double), ("ghost_setup_ms", C.c_double),
                 ("rhs_bytes_per_node", C.c_double), ("rhs_flops_per_node", C.c_double),
                 ("persist_lanes", C.c_int32), ("persist_regs", C.c_int32), ("persist_chunk", C.c_int32),
-                ("persist_halo_max", C.c_int32)]
+                ("persist_halo_max", C.c_int32), ("persist_ctas", C.c_int32), ("reserved2", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -95,7 +95,7 @@ SIGNATURES = [
     ("rbf_rk4_step", C.c_int, [_P, _D, _D, _P]),
     ("rbf_run", C.c_int, [_P, _D, _D, _I64, _P]),
     ("rbf_run_host", C.c_int, [_P, _D, _D, _I64, _P]),
-    ("rbf_set_run_mode", C.c_int, [_P, _I32, _I32]),
+    ("rbf_set_run_mode", C.c_int, [_P, _I32, _I32, _I32]),
     ("rbf_set_spin_limit", C.c_int, [_P, _I64]),
     ("rbf_sync", C.c_int, [_P]),
     ("rbf_minmax", C.c_int, [_P, _P, _P]),
@@ -228,9 +228,9 @@ class Problem:
 
     RUN_MODES = {"auto": 0, "graph": 1, "persistent": 2}
 
-    def set_run_mode(self, mode, lanes=0):
+    def set_run_mode(self, mode, lanes=0, ctas=0):
         """'graph', 'persistent' or 'auto' (see rbf_set_run_mode)."""
-        _check(lib().rbf_set_run_mode(self._h, self.RUN_MODES[mode], int(lanes)))
+        _check(lib().rbf_set_run_mode(self._h, self.RUN_MODES[mode], int(lanes), int(ctas)))
 
     def set_spin_limit(self, polls):
         _check(lib().rbf_set_spin_limit(self._h, int(polls)))

@@ -57,4 +57,4 @@ def test_struct_layouts_match_header():
     # 8 int32 + 8 doubles; 6 int32 + 2 doubles; see include/rbffd.h
     assert C.sizeof(rbffd.NSParams) == 8 * 4 + 8 * 8
     assert C.sizeof(rbffd.AdvParams) == 6 * 4 + 2 * 8
-    assert C.sizeof(rbffd.Info) == 3 * 8 + 10 * 4 + 4 * 8 + 4 * 4
+    assert C.sizeof(rbffd.Info) == 3 * 8 + 10 * 4 + 4 * 8 + 6 * 4
