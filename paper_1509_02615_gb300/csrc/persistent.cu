@@ -153,7 +153,7 @@ struct CtaInfo {
     int32_t n_set;      // weight sets per wall row
     int32_t n_coef;     // band coefficients of all its pairs
     int32_t row_pad;    // row stride of the slot-major row arrays (bank-conflict free)
-    int32_t pad_;
+    int32_t pair_pad;   // pair stride of the coefficient arrays (bank-conflict free)
     int64_t blob_off;   // byte offset of its constant block
     int32_t blob_bytes;
     int32_t o_rw, o_rinfo, o_gc, o_cidx, o_cval;   // sections of the block (row slots at 0)
@@ -327,15 +327,19 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
                 const int M = lanes_for(ci.n_gc, blockDim.x, kPairLanes);
                 const int npl = (ci.n_gc * M + 31) & ~31;
                 for (int e = threadIdx.x; e < npl; e += blockDim.x) {
-                    const int k = e / M, ln = e % M;
-                    const int4 gc = gcs[k < ci.n_gc ? k : ci.n_gc - 1];   // position, field mask, first, count
+                    const int k0 = e / M, ln = e % M;
+                    const int k = k0 < ci.n_gc ? k0 : ci.n_gc - 1;
+                    const int4 gc = gcs[k];   // list position, field mask, -, count
                     T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-                    const uint16_t *cj = cidx + gc.z;
-                    const T *cv = cval + gc.z;
+                    // pair-interleaved [coefficient][pair_pad]: the lanes of a warp
+                    // read consecutive pairs
+                    const size_t PP = ci.pair_pad;
+                    const uint16_t *cj = cidx + k;
+                    const T *cv = cval + k;
 #pragma unroll 4
                     for (int j = ln; j < gc.w; j += M) {
-                        const T c = cv[j];
-                        const int rr = cj[j];
+                        const T c = cv[j * PP];
+                        const int rr = cj[j * PP];
                         if (gc.y & 1) s0 += c * res[rr];
                         if (gc.y & 2) s1 += c * res[ci.n_rows + rr];
                         if (gc.y & 4) s2 += c * res[2 * ci.n_rows + rr];
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
                         s2 += __shfl_xor_sync(0xffffffffu, s2, o, M);
                         s3 += __shfl_xor_sync(0xffffffffu, s3, o, M);
                     }
-                    if (k < ci.n_gc) {
+                    if (k0 < ci.n_gc) {
 #pragma unroll
                         for (int f = 0; f < 4; ++f)
                             if (f % M == ln && (gc.y & (1 << f)))
@@ -789,33 +793,47 @@ bool persistent_plan(Problem &pb, int G, int ctas) {
             }
             ci.o_rinfo = (int32_t)align16(b.size());
             put(b, ci.o_rinfo, ri.data(), ri.size() * 4);
-            // (ghost, class) pairs and their band coefficients
-            std::vector<int32_t> gcv;
-            std::vector<uint16_t> cix;
-            std::vector<unsigned char> cvl;
-            for (int32_t gr : ghosts) {
-                const int64_t q = posv[gr - P];
+            // (ghost, class) pairs and their band coefficients, pair-interleaved
+            // [coefficient j][pair_pad] with the lane groups of a warp in distinct banks
+            std::vector<std::pair<int32_t, int32_t>> pairs;   // (ghost record, class)
+            size_t maxlen = 0, ncoef = 0;
+            for (int32_t gr : ghosts)
                 for (int cl = 0; cl < gh.n_class; ++cl) {
                     if (!cls_fields[cl]) continue;
-                    const auto &bd = band[(size_t)cl * ng + q];
-                    gcv.push_back(loc[gr]);
-                    gcv.push_back(cls_fields[cl]);
-                    gcv.push_back((int32_t)cix.size());
-                    gcv.push_back((int32_t)bd.size());
-                    for (auto &e : bd) {
-                        cix.push_back((uint16_t)rloc[e.first]);
-                        if (pb.precision == 64) {
-                            const double v = e.second;
-                            cvl.insert(cvl.end(), (const unsigned char *)&v, (const unsigned char *)&v + 8);
-                        } else {
-                            const float v = (float)e.second;   // exact: the inverse is stored in FP32
-                            cvl.insert(cvl.end(), (const unsigned char *)&v, (const unsigned char *)&v + 4);
-                        }
+                    pairs.emplace_back(gr, cl);
+                    const size_t len = band[(size_t)cl * ng + posv[gr - P]].size();
+                    maxlen = std::max(maxlen, len);
+                    ncoef += len;
+                }
+            const int n_gc = (int)pairs.size();
+            const int Mp = lanes_for(n_gc, threads, kPairLanes);
+            int PPd = std::max(n_gc, 1);
+            while (PPd % 32 != (32 / Mp) % 32) ++PPd;
+            ci.pair_pad = PPd;
+            std::vector<int32_t> gcv;
+            std::vector<uint16_t> cix(maxlen * PPd, 0);
+            std::vector<unsigned char> cvl(maxlen * PPd * ts, 0);
+            for (int k = 0; k < n_gc; ++k) {
+                const int32_t gr = pairs[k].first;
+                const int cl = pairs[k].second;
+                const auto &bd = band[(size_t)cl * ng + posv[gr - P]];
+                gcv.push_back(loc[gr]);
+                gcv.push_back(cls_fields[cl]);
+                gcv.push_back(0);
+                gcv.push_back((int32_t)bd.size());
+                for (size_t j = 0; j < bd.size(); ++j) {
+                    cix[j * PPd + k] = (uint16_t)rloc[bd[j].first];
+                    if (pb.precision == 64) {
+                        const double v = bd[j].second;
+                        memcpy(cvl.data() + (j * PPd + k) * 8, &v, 8);
+                    } else {
+                        const float v = (float)bd[j].second;   // exact: the inverse is stored in FP32
+                        memcpy(cvl.data() + (j * PPd + k) * 4, &v, 4);
                     }
                 }
             }
-            ci.n_gc = (int32_t)(gcv.size() / 4);
-            ci.n_coef = (int32_t)cix.size();
+            ci.n_gc = n_gc;
+            ci.n_coef = (int32_t)ncoef;
             ci.o_gc = (int32_t)align16(b.size());
             put(b, ci.o_gc, gcv.data(), gcv.size() * 4);
             ci.o_cidx = (int32_t)align16(b.size());
