@@ -729,8 +729,27 @@ int rbf_learned_run(rbf_mlp *h, double t0, double dt, int64_t n_steps, const dou
         const float4 al = make_float4((float)alpha[0], (float)alpha[1], (float)alpha[2], (float)alpha[3]);
         Mlp &m = h->impl;
         rbf::Problem &pb = h->coarse->impl;
-        rbf::DevBuf<unsigned char> delta((size_t)pb.n_prog * 4 * pb.tsize());
         RBF_CUDA(cudaMemsetAsync(m.bad.p, 0, sizeof(unsigned long long), pb.st));
+        if (pb.run_mode == RBF_RUN_PERSISTENT && rbf::persistent_mlp_ready(pb)) {
+            // the whole corrected run in one persistent launch (network evaluated
+            // at stage 0 of every step from the records in shared memory)
+            rbf::MlpView mv{};
+            mv.Pb = m.Pb.p;
+            mv.P = m.P.p;
+            mv.oW1 = m.oW1; mv.ob1 = m.ob1; mv.oW2 = m.oW2; mv.ob2 = m.ob2; mv.oW3 = m.oW3; mv.ob3 = m.ob3;
+            mv.scales = m.scales.p;
+            for (int f = 0; f < 4; ++f) mv.alpha[f] = (float)alpha[f];
+            mv.n_in = m.n_in;
+            mv.bad = m.bad.p;
+            rbf::persistent_run_mlp(pb, dt, n_steps, U, pb.st, mv);
+            unsigned long long bad = 0;
+            RBF_CUDA(cudaMemcpyAsync(&bad, m.bad.p, sizeof(bad), cudaMemcpyDeviceToHost, pb.st));
+            RBF_CUDA(cudaStreamSynchronize(pb.st));
+            rbf::persistent_check(pb);
+            if (n_fallback) *n_fallback = (int64_t)bad;
+            return;
+        }
+        rbf::DevBuf<unsigned char> delta((size_t)pb.n_prog * 4 * pb.tsize());
         for (int64_t s = 0; s < n_steps; ++s) {
             // features need the ghosts of the current state; then step and add dt * delta
             rbf::enqueue_ghost_fill(pb, U, pb.st);

@@ -21,6 +21,15 @@
 // (every field of an operator class at once; the lanes per row and per
 // ghost are chosen so that one pass of the CTA's threads covers them).
 //
+// Learned correction (a9, MLP variants): at stage 0 of every step the CTA's
+// shared memory holds the step-start records of its stencils, ghosts
+// included -- exactly the network's inputs.  Each CTA evaluates the network
+// for its own nodes -- layers 1 and 2 on the tensor cores (mma.sync, BF16
+// weights; features and activations as two BF16 terms hi + lo, i.e. 16
+// significant bits; FP32 accumulation), layer 3 in FP32 -- and adds
+// alpha dt delta in the stage-3 epilogue, so the correction costs no extra
+// barrier.
+//
 // One stage per CTA: copy the listed records of the stage input into
 // shared memory (its own nodes' from registers, the others in one round of
 // independent L2 loads), solve its ghosts,
@@ -28,6 +37,8 @@
 // and meet every other CTA at a grid barrier.  Every barrier wait is
 // bounded: after spin_limit polls a CTA raises the abort flag, every CTA
 // leaves at its next barrier, and the host reports RBF_E_TIMEOUT.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -181,7 +192,110 @@ struct PArgs {
     unsigned base;                  // its value when this launch starts
     int *abort;
     long long spin_limit;
+    // a9 (MLP variants): network, scales, strengths
+    const __nv_bfloat16 *mW;        // BF16 parameters (W1 at oW1, W2 at oW2, W3 at oW3)
+    const float *mP;                // FP32 parameters (biases)
+    int64_t oW1, ob1, oW2, ob2, oW3, ob3;
+    const float *mscales;
+    float4 malpha;
+    float mdt;
+    int n_in, mslots;
+    unsigned long long *mbad;
 };
+
+constexpr int kWidth = 64;     // hidden width of the learned correction's network
+constexpr float kClip = 4.f;   // |f(x) - f(0)| <= 4 output scales
+
+// Shared-memory layout of the network and its work arrays (MLP variants),
+// identical on host and device.  NB nodes per chunk (a multiple of 16, the
+// tensor-core tile height).  Weights are stored transposed ([unit][input],
+// input padded by 8 so that the fragment loads of a warp hit distinct banks);
+// features and layer-1 outputs as two BF16 terms (hi + lo) per value.
+struct MlpLayout {
+    int k1, kp1, kp2;   // layer-1 inputs padded to 16, row strides
+    size_t w1t, w2t, w3, b, xh, xl, hh, hl, h2, d, sl, end;
+};
+__host__ __device__ inline int mlp_nb(int chunk) {
+    const int nb = (chunk + 15) & ~15;   // a CTA's nodes in one pass when they fit 64
+    return nb > 64 ? 64 : nb;
+}
+__host__ __device__ inline MlpLayout mlp_layout(int n_in, int chunk, int slots) {
+    MlpLayout L;
+    const int nb = mlp_nb(chunk);
+    L.k1 = (n_in + 15) & ~15;
+    L.kp1 = L.k1 + 8;
+    L.kp2 = kWidth + 8;
+    L.w1t = 0;
+    L.w2t = align16(L.w1t + (size_t)kWidth * L.kp1 * 2);
+    L.w3 = align16(L.w2t + (size_t)kWidth * L.kp2 * 2);
+    L.b = align16(L.w3 + (size_t)kWidth * 4 * 2);
+    L.xh = align16(L.b + (size_t)(4 * kWidth + 8) * 4);         // b1, b2, b3, f(0), scratch
+    L.xl = align16(L.xh + (size_t)nb * L.kp1 * 2);
+    L.hh = align16(L.xl + (size_t)nb * L.kp1 * 2);
+    L.hl = align16(L.hh + (size_t)nb * L.kp2 * 2);
+    L.h2 = align16(L.hl + (size_t)nb * L.kp2 * 2);
+    L.d = align16(L.h2 + (size_t)kWidth * nb * 4);
+    L.sl = align16(L.d + (size_t)chunk * 4 * 4);                 // stencil list positions [chunk][slots]
+    L.end = align16(L.sl + (size_t)chunk * slots * 2);
+    return L;
+}
+
+__device__ __forceinline__ uint32_t ld32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+// D += A B on the tensor cores: A 16 x 16 (row), B 16 x 8 (col), BF16 in, FP32 out
+__device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// x as hi + lo, two BF16 values (16 significant bits of x)
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));
+}
+
+// One dense layer on the tensor cores: out[n][j] = tanh(bias[j] + sum_k in[n][k] W[k][j])
+// for NB rows, 64 units, K inputs; in as (hi, lo) BF16 rows of stride kp, W
+// transposed [j][k] with stride kpw.  A warp takes a 16-row block and half
+// the units: four independent 16 x 8 accumulators share each A fragment.
+template <class Store>
+__device__ __forceinline__ void mma_layer(const __nv_bfloat16 *xh, const __nv_bfloat16 *xl, int kp,
+                                          const __nv_bfloat16 *wt, int kpw, int K, const float *bias, int NB,
+                                          Store store) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int grp = lane >> 2, qd = lane & 3;
+    for (int item = wid; item < (NB / 16) * 2; item += nw) {
+        const int mt = item >> 1, half = item & 1;
+        const int r0 = mt * 16 + grp;
+        float d[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) d[u][0] = d[u][1] = d[u][2] = d[u][3] = 0.f;
+        for (int k = qd * 2; k < K; k += 16) {
+            const uint32_t ah[4] = {ld32(xh + r0 * kp + k), ld32(xh + (r0 + 8) * kp + k), ld32(xh + r0 * kp + k + 8),
+                                    ld32(xh + (r0 + 8) * kp + k + 8)};
+            const uint32_t al[4] = {ld32(xl + r0 * kp + k), ld32(xl + (r0 + 8) * kp + k), ld32(xl + r0 * kp + k + 8),
+                                    ld32(xl + (r0 + 8) * kp + k + 8)};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int nn = (half * 4 + u) * 8 + grp;
+                const uint32_t b0 = ld32(wt + nn * kpw + k), b1 = ld32(wt + nn * kpw + k + 8);
+                mma_bf16(d[u], ah, b0, b1);
+                mma_bf16(d[u], al, b0, b1);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = (half * 4 + u) * 8 + qd * 2;
+            store(r0, j, tanhf(d[u][0] + bias[j]));
+            store(r0, j + 1, tanhf(d[u][1] + bias[j + 1]));
+            store(r0 + 8, j, tanhf(d[u][2] + bias[j]));
+            store(r0 + 8, j + 1, tanhf(d[u][3] + bias[j + 1]));
+        }
+    }
+}
 
 constexpr int kRowLanes = 8;    // most lanes per wall row in the residuals
 constexpr int kPairLanes = 8;   // most lanes per (ghost, class) pair in the ghost values
@@ -194,7 +308,94 @@ __host__ __device__ __forceinline__ int lanes_for(int items, int threads, int mo
     return l;
 }
 
-template <class T, int G, int R, int MAXT>
+// a9 at stage 0: delta of the CTA's own nodes from the records in shared
+// memory.  Features as the stand-alone inference kernel: 4 (n-1) scaled
+// stencil differences (field-major rows of W1) and the node's 4 scaled
+// values.  Layers 1 and 2 on the tensor cores, layer 3 and the correction in
+// FP32.
+template <class T>
+__device__ void mlp_phase(const PArgs<T> &a, const T *halo, const int32_t *hl, const MlpLayout &ML,
+                          unsigned char *mreg, int n_own, int NB) {
+    if constexpr (sizeof(T) == 4) {
+        const int slots = a.mslots;
+        const __nv_bfloat16 *sW1t = reinterpret_cast<const __nv_bfloat16 *>(mreg + ML.w1t);
+        const __nv_bfloat16 *sW2t = reinterpret_cast<const __nv_bfloat16 *>(mreg + ML.w2t);
+        const __nv_bfloat16 *sW3 = reinterpret_cast<const __nv_bfloat16 *>(mreg + ML.w3);
+        const float *sb = reinterpret_cast<const float *>(mreg + ML.b);
+        __nv_bfloat16 *Xh = reinterpret_cast<__nv_bfloat16 *>(mreg + ML.xh);
+        __nv_bfloat16 *Xl = reinterpret_cast<__nv_bfloat16 *>(mreg + ML.xl);
+        __nv_bfloat16 *Hh = reinterpret_cast<__nv_bfloat16 *>(mreg + ML.hh);
+        __nv_bfloat16 *Hl = reinterpret_cast<__nv_bfloat16 *>(mreg + ML.hl);
+        float *H2 = reinterpret_cast<float *>(mreg + ML.h2);
+        float *sD = reinterpret_cast<float *>(mreg + ML.d);
+        const uint16_t *sL = reinterpret_cast<const uint16_t *>(mreg + ML.sl);
+        const float is[4] = {1.f / a.mscales[0], 1.f / a.mscales[1], 1.f / a.mscales[2], 1.f / a.mscales[3]};
+        const int kp1 = ML.kp1, kp2 = ML.kp2;
+        for (int c0 = 0; c0 < n_own; c0 += NB) {
+            const int nb = min(NB, n_own - c0);
+            // features [node][column] as hi + lo: P lanes per node (a power of two),
+            // one (node, slot) at a time, all four fields
+            int P = 1;
+            while (P < 8 && NB * P * 2 <= (int)blockDim.x) P <<= 1;
+            for (int e = threadIdx.x; e < NB * P; e += blockDim.x)
+            for (int t = e % P; t <= slots; t += P) {
+                const int n = e / P;
+                float x[4] = {0.f, 0.f, 0.f, 0.f};
+                if (n < nb) {
+                    const Rec<T> own = sh_rec(halo, c0 + n);
+                    if (t < slots) {
+                        const Rec<T> r = sh_rec(halo, sL[(c0 + n) * slots + t]);
+                        x[0] = (float)(r.u - own.u) * is[0];
+                        x[1] = (float)(r.w - own.w) * is[1];
+                        x[2] = (float)(r.t - own.t) * is[2];
+                        x[3] = (float)(r.p - own.p) * is[3];
+                    } else {   // the node's own values
+                        x[0] = (float)own.u / a.mscales[8];
+                        x[1] = (float)own.w / a.mscales[9];
+                        x[2] = (float)own.t / a.mscales[10];
+                        x[3] = (float)own.p / a.mscales[11];
+                    }
+                }
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    const int c = t < slots ? f * slots + t : 4 * slots + f;
+                    split_bf16(x[f], Xh[n * kp1 + c], Xl[n * kp1 + c]);
+                }
+            }
+            __syncthreads();
+            // layer 1: tanh(b1 + x W1) as hi + lo
+            mma_layer(Xh, Xl, kp1, sW1t, kp1, ML.k1, sb, NB, [&](int r, int j, float v) {
+                split_bf16(v, Hh[r * kp2 + j], Hl[r * kp2 + j]);
+            });
+            __syncthreads();
+            // layer 2: tanh(b2 + h W2), FP32 [unit][node]
+            mma_layer(Hh, Hl, kp2, sW2t, kp2, kWidth, sb + kWidth, NB,
+                      [&](int r, int j, float v) { H2[j * NB + r] = v; });
+            __syncthreads();
+            // layer 3 and the correction: one thread per (node, field)
+            for (int e = threadIdx.x; e < nb * 4; e += blockDim.x) {
+                const int n = e / 4, cf = e % 4;
+                float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;   // four partial sums over m mod 4
+#pragma unroll 4
+                for (int m = 0; m < kWidth; m += 4) {
+                    p0 += H2[m * NB + n] * __bfloat162float(sW3[m * 4 + cf]);
+                    p1 += H2[(m + 1) * NB + n] * __bfloat162float(sW3[(m + 1) * 4 + cf]);
+                    p2 += H2[(m + 2) * NB + n] * __bfloat162float(sW3[(m + 2) * 4 + cf]);
+                    p3 += H2[(m + 3) * NB + n] * __bfloat162float(sW3[(m + 3) * 4 + cf]);
+                }
+                const float y = sb[2 * kWidth + cf] + ((p0 + p1) + (p2 + p3));
+                // y = f(x) - f(0), clipped at 4 output scales
+                float d = fminf(fmaxf(y - sb[2 * kWidth + 4 + cf], -kClip), kClip) * a.mscales[4 + cf];
+                const unsigned char fl = __ldg(a.flags + hl[c0 + n]);
+                if ((cf == 1 && (fl & 1)) || (cf == 0 && (fl & 2))) d = 0.f;   // Dirichlet components stay fixed
+                sD[(c0 + n) * 4 + cf] = d;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <class T, int G, int R, int MAXT, bool MLP>
 __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant__ PArgs<T> a) {
     using P = PV<T>;
     using W = typename P::W;
@@ -219,6 +420,63 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
     const uint16_t *cidx = reinterpret_cast<const uint16_t *>(blob + ci.o_cidx);
     const T *cval = reinterpret_cast<const T *>(blob + ci.o_cval);
     const int32_t *hl = a.hlist + ci.list_off;
+
+    // a9: the network in shared memory and f(0) (MLP variants)
+    unsigned char *mreg = blob + align16(ci.blob_bytes);
+    const MlpLayout ML = mlp_layout(a.n_in, a.chunk, a.mslots);
+    const int NB = mlp_nb(a.chunk);
+    if constexpr (MLP) {
+        __nv_bfloat16 *sW1t = reinterpret_cast<__nv_bfloat16 *>(mreg + ML.w1t);
+        __nv_bfloat16 *sW2t = reinterpret_cast<__nv_bfloat16 *>(mreg + ML.w2t);
+        __nv_bfloat16 *sW3 = reinterpret_cast<__nv_bfloat16 *>(mreg + ML.w3);
+        float *sb = reinterpret_cast<float *>(mreg + ML.b);   // b1, b2, b3, f(0), scratch [128]
+        __nv_bfloat16 *Xh = reinterpret_cast<__nv_bfloat16 *>(mreg + ML.xh);
+        __nv_bfloat16 *Xl = reinterpret_cast<__nv_bfloat16 *>(mreg + ML.xl);
+        uint16_t *sL = reinterpret_cast<uint16_t *>(mreg + ML.sl);
+        const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+        for (int e = threadIdx.x; e < kWidth * ML.kp1; e += blockDim.x) {
+            const int j = e / ML.kp1, c = e % ML.kp1;
+            sW1t[e] = c < a.n_in ? a.mW[a.oW1 + (int64_t)c * kWidth + j] : zero;
+        }
+        for (int e = threadIdx.x; e < kWidth * ML.kp2; e += blockDim.x) {
+            const int j = e / ML.kp2, m = e % ML.kp2;
+            sW2t[e] = m < kWidth ? a.mW[a.oW2 + (int64_t)m * kWidth + j] : zero;
+        }
+        for (int e = threadIdx.x; e < kWidth * 4; e += blockDim.x) sW3[e] = a.mW[a.oW3 + e];
+        for (int e = threadIdx.x; e < kWidth; e += blockDim.x) {
+            sb[e] = a.mP[a.ob1 + e];
+            sb[kWidth + e] = a.mP[a.ob2 + e];
+        }
+        if (threadIdx.x < 4) sb[2 * kWidth + threadIdx.x] = a.mP[a.ob3 + threadIdx.x];
+        // padded feature columns stay zero
+        for (int e = threadIdx.x; e < NB * ML.kp1; e += blockDim.x) Xh[e] = Xl[e] = zero;
+        // list position of every stencil slot of the own nodes (constant over the run)
+        const int GV = (int)(a.total / ((int64_t)a.SLQ * a.lanes)), Vv = 16 / (int)sizeof(T), Gl = GV / Vv;
+        for (int e = threadIdx.x; e < ci.n_own * a.mslots; e += blockDim.x) {
+            const int n = e / a.mslots, t = e % a.mslots;
+            const int q = t / GV, gl = (t / Vv) % Gl, v = t % Vv;
+            const int64_t p = (int64_t)blockIdx.x * a.chunk + n;
+            sL[e] = __ldg(a.lidx + (((int64_t)q * a.lanes + p) * Gl + gl) * Vv + v);
+        }
+        __syncthreads();
+        // f(0): the network's output for all-zero features
+        float *z1 = sb + 2 * kWidth + 8, *z2 = z1 + kWidth;
+        for (int t = threadIdx.x; t < kWidth; t += blockDim.x) z1[t] = tanhf(sb[t]);
+        __syncthreads();
+        for (int t = threadIdx.x; t < kWidth; t += blockDim.x) {
+            float acc = sb[kWidth + t];
+            for (int m = 0; m < kWidth; ++m) acc += z1[m] * __bfloat162float(sW2t[t * ML.kp2 + m]);
+            z2[t] = tanhf(acc);
+        }
+        __syncthreads();
+        if (threadIdx.x < 4) {
+            float acc = sb[2 * kWidth + threadIdx.x];
+            for (int m = 0; m < kWidth; ++m) acc += z2[m] * __bfloat162float(sW3[m * 4 + threadIdx.x]);
+            sb[2 * kWidth + 4 + threadIdx.x] = acc;
+        }
+        __syncthreads();
+    }
+    const float *sD = reinterpret_cast<const float *>(mreg + ML.d);   // corrections of the own nodes
 
     const int li = threadIdx.x / G, g = threadIdx.x % G;
     const bool live = li < ci.n_own;
@@ -360,6 +618,9 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
                 }
                 __syncthreads();
             }
+            if constexpr (MLP) {
+                if (st == 0) mlp_phase(a, halo, hl, ML, mreg, ci.n_own, NB);
+            }
             // ---- stencil sums, tendencies, RK4 update ----------------------------
             Rec<T> fi = {0, 0, 0, 0};
             if (DIFF) fi = sh_rec(halo, self);
@@ -425,6 +686,18 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
                     o4[f] = un[f] + (K[f] + bs * kf);
                 }
             }
+            if constexpr (MLP) {
+                if (st == 3 && live) {
+                    // U += alpha dt delta; a non-finite correction is skipped and counted
+                    const float al[4] = {a.malpha.x, a.malpha.y, a.malpha.z, a.malpha.w};
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        const T d = (T)sD[li * 4 + f];
+                        if (isfinite((double)d)) o4[f] += (T)al[f] * (T)a.mdt * d;
+                        else if (g == 0) atomicAdd(a.mbad, 1ull);
+                    }
+                }
+            }
             if (st == 3) {
 #pragma unroll
                 for (int f = 0; f < 4; ++f) un[f] = o4[f];
@@ -442,20 +715,25 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
 // stage.  Thread limits keep each variant within the register file.
 struct Variant {
     int G, R, maxt;
+    bool mlp;
     void *fn;
 };
 
 template <class T>
 std::vector<Variant> variants() {
     if constexpr (sizeof(T) == 4) {
-        return {{1, 9, 256, (void *)rk4_persistent<float, 1, 9, 256>},
-                {1, 0, 512, (void *)rk4_persistent<float, 1, 0, 512>},
-                {2, 0, 512, (void *)rk4_persistent<float, 2, 0, 512>},
-                {4, 0, 1024, (void *)rk4_persistent<float, 4, 0, 1024>}};
+        return {{1, 9, 256, false, (void *)rk4_persistent<float, 1, 9, 256, false>},
+                {1, 0, 512, false, (void *)rk4_persistent<float, 1, 0, 512, false>},
+                {2, 0, 512, false, (void *)rk4_persistent<float, 2, 0, 512, false>},
+                {4, 0, 1024, false, (void *)rk4_persistent<float, 4, 0, 1024, false>},
+                {1, 9, 256, true, (void *)rk4_persistent<float, 1, 9, 256, true>},
+                {1, 0, 512, true, (void *)rk4_persistent<float, 1, 0, 512, true>},
+                {2, 0, 512, true, (void *)rk4_persistent<float, 2, 0, 512, true>},
+                {4, 0, 512, true, (void *)rk4_persistent<float, 4, 0, 512, true>}};
     } else {
-        return {{1, 0, 512, (void *)rk4_persistent<double, 1, 0, 512>},
-                {2, 0, 512, (void *)rk4_persistent<double, 2, 0, 512>},
-                {4, 0, 1024, (void *)rk4_persistent<double, 4, 0, 1024>}};
+        return {{1, 0, 512, false, (void *)rk4_persistent<double, 1, 0, 512, false>},
+                {2, 0, 512, false, (void *)rk4_persistent<double, 2, 0, 512, false>},
+                {4, 0, 1024, false, (void *)rk4_persistent<double, 4, 0, 1024, false>}};
     }
 }
 
@@ -504,7 +782,15 @@ PArgs<T> pargs(Problem &pb, T *U, double dt, int64_t n_steps) {
 void *variant_fn(const PersistPlan &ps, int precision) {
     const std::vector<Variant> v = precision == 64 ? variants<double>() : variants<float>();
     for (const Variant &x : v)
-        if (x.G == ps.G && x.R == ps.R && x.maxt == ps.maxt) return x.fn;
+        if (!x.mlp && x.G == ps.G && x.R == ps.R && x.maxt == ps.maxt) return x.fn;
+    return nullptr;
+}
+
+// MLP variant for the plan's lanes and register residency, if any
+void *mlp_variant_fn(const PersistPlan &ps, int precision) {
+    if (precision != 32) return nullptr;
+    for (const Variant &x : variants<float>())
+        if (x.mlp && x.G == ps.G && x.R == ps.R && ps.threads <= x.maxt) return x.fn;
     return nullptr;
 }
 
@@ -854,7 +1140,7 @@ bool persistent_plan(Problem &pb, int G, int ctas) {
     int pick = -1;
     for (int k = 0; k < (int)vs.size(); ++k) {
         const Variant &v = vs[k];
-        if (v.G != G || threads > v.maxt) continue;
+        if (v.mlp || v.G != G || threads > v.maxt) continue;
         if (v.R > 0 && SLQ > v.R) continue;
         if (pick < 0 || (v.R > 0 && vs[pick].R == 0)) pick = k;
     }
@@ -912,6 +1198,37 @@ void persistent_run(Problem &pb, double dt, int64_t n_steps, void *U, cudaStream
         RBF_CUDA(cudaLaunchCooperativeKernel(fn, dim3(ps.grid), dim3(ps.threads), args, ps.smem, s));
     }
     // one barrier after every stage but the last
+    ps.base += (unsigned)((uint64_t)ps.grid * (uint64_t)(4 * n_steps - 1));
+}
+
+bool persistent_mlp_ready(const Problem &pb) {
+    return pb.kind == kNS && pb.precision == 32 && pb.ps.ready && pb.diff == 1 && mlp_variant_fn(pb.ps, 32) != nullptr;
+}
+
+void persistent_run_mlp(Problem &pb, double dt, int64_t n_steps, void *U, cudaStream_t s, const MlpView &mv) {
+    PersistPlan &ps = pb.ps;
+    RBF_REQUIRE(persistent_mlp_ready(pb), "no persistent kernel with the network for this problem");
+    RBF_REQUIRE(mv.n_in == 4 * pb.n_slots + 4, "network inputs %d do not match the stencil", mv.n_in);
+    if (n_steps <= 0) return;
+    void *fn = mlp_variant_fn(ps, 32);
+    int smem_optin = 0, dev = 0;
+    RBF_CUDA(cudaGetDevice(&dev));
+    RBF_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t smem = ps.smem + mlp_layout(mv.n_in, ps.chunk, pb.n_slots).end;
+    RBF_REQUIRE(smem <= (size_t)smem_optin, "network does not fit shared memory beside the record lists");
+    RBF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    PArgs<float> a = pargs<float>(pb, (float *)U, dt, n_steps);
+    a.mW = reinterpret_cast<const __nv_bfloat16 *>(mv.Pb);
+    a.mP = mv.P;
+    a.oW1 = mv.oW1; a.ob1 = mv.ob1; a.oW2 = mv.oW2; a.ob2 = mv.ob2; a.oW3 = mv.oW3; a.ob3 = mv.ob3;
+    a.mscales = mv.scales;
+    a.malpha = make_float4(mv.alpha[0], mv.alpha[1], mv.alpha[2], mv.alpha[3]);
+    a.mdt = (float)dt;
+    a.n_in = mv.n_in;
+    a.mslots = pb.n_slots;
+    a.mbad = mv.bad;
+    void *args[] = {&a};
+    RBF_CUDA(cudaLaunchCooperativeKernel(fn, dim3(ps.grid), dim3(ps.threads), args, smem, s));
     ps.base += (unsigned)((uint64_t)ps.grid * (uint64_t)(4 * n_steps - 1));
 }
 

@@ -160,6 +160,22 @@ double ensemble_node_updates(const Problem &pb, int64_t max_steps);
 // tells the same).
 bool persistent_plan(Problem &pb, int G, int ctas);
 void persistent_run(Problem &pb, double dt, int64_t n_steps, void *U, cudaStream_t s);
+
+// a9 fused into the persistent run: the learned correction's network (BF16
+// weights, FP32 biases and scales) and its per-field strengths.
+struct MlpView {
+    const void *Pb;                 // __nv_bfloat16 parameters
+    const float *P;                 // FP32 parameters (biases)
+    int64_t oW1, ob1, oW2, ob2, oW3, ob3;
+    const float *scales;            // [12]: feature, output, own-value scales
+    float alpha[4];
+    int n_in;
+    unsigned long long *bad;        // non-finite corrections skipped
+};
+// True if a learned run can go through the persistent kernel (FP32 problem in
+// persistent mode with a variant that holds the network).
+bool persistent_mlp_ready(const Problem &pb);
+void persistent_run_mlp(Problem &pb, double dt, int64_t n_steps, void *U, cudaStream_t s, const MlpView &mv);
 // RBF_E_TIMEOUT (and clears the flag) if a persistent launch gave up a wait.
 void persistent_check(Problem &pb);
 

@@ -1,0 +1,82 @@
+"""a9 fused into the persistent run: a corrected coarse run in one launch
+(the network evaluated at stage 0 of every step from the CTA's records in
+shared memory) against the stand-alone path (ghost fill, inference kernel,
+RK4 step, apply kernel per step), which the oracle pins at 1e-4.
+
+Tolerances: with all strengths zero the fused run is bitwise the plain
+persistent run; with nonzero strengths it agrees with the stand-alone path
+to 1e-5 relative l2 per field after 40 steps (FP32 sums taken in another
+order: layer 1 field-major, ghost values from the banded inverse rows).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_1509_02615_gb300 import inputs as inp  # noqa: E402
+from paper_1509_02615_gb300 import learned  # noqa: E402
+from paper_1509_02615_gb300 import rbffd  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1509_02615_gb300 import _build
+    _build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+SCALES = np.array([2.0, 1.5, 0.5, 2e-4, 0.1, 0.05, 0.02, 1e-5, 4.0, 3.0, 6.0, 1e-3], np.float32)
+
+
+def _setup(h, lanes, ctas):
+    nodes = inp.density_current_nodes(h)
+    pb = rbffd.ns_problem(nodes, precision=32, threads_per_node=lanes)
+    mlp = rbffd.Mlp(pb)
+    mlp.set_params(learned.init_params(4 * 36 + 4, seed=7))
+    mlp.set_scales(SCALES)
+    pb.set_run_mode("persistent", lanes=lanes, ctas=ctas)
+    U0 = inp.perturbed_density_current(nodes, 3)
+    return nodes, pb, mlp, U0
+
+
+@pytest.mark.parametrize("h,lanes,ctas", [(800.0, 1, 0), (400.0, 4, 38), (400.0, 2, 76)])
+def test_fused_learned_run_matches_standalone(h, lanes, ctas):
+    nodes, pb, mlp, U0 = _setup(h, lanes, ctas)
+    dt, steps, alpha = h / 400.0, 40, (0.5, 0.5, 1.0, 0.25)
+    A = rbffd.state_tensor(U0, 32)
+    nf = mlp.run(0.0, dt, steps, A, alpha=alpha)            # persistent mode: fused
+    pb.set_run_mode("graph")
+    B = rbffd.state_tensor(U0, 32)
+    nb = mlp.run(0.0, dt, steps, B, alpha=alpha)            # stand-alone kernels
+    P = nodes.n_prog
+    a, b = rbffd.fields(A)[:, :P], rbffd.fields(B)[:, :P]
+    errs = [rel(a[f], b[f]) for f in range(4)]
+    # the correction is visible: the corrected run differs from the plain one
+    C = rbffd.state_tensor(U0, 32)
+    pb.run(0.0, dt, steps, C)
+    pb.sync()
+    c = rbffd.fields(C)[:, :P]
+    effect = [rel(b[f], c[f]) for f in range(4)]
+    print(f"h={h} lanes={lanes}: fused vs stand-alone {['%.1e' % e for e in errs]}; "
+          f"correction effect {['%.1e' % e for e in effect]}")
+    assert nf == 0 and nb == 0
+    assert max(errs) < 1e-5, errs
+    assert min(effect) > 100 * max(errs)
+
+
+def test_fused_zero_strength_is_the_plain_run():
+    nodes, pb, mlp, U0 = _setup(400.0, 4, 0)
+    A = rbffd.state_tensor(U0, 32)
+    mlp.run(0.0, 1.0, 25, A, alpha=(0.0, 0.0, 0.0, 0.0))
+    B = rbffd.state_tensor(U0, 32)
+    pb.run(0.0, 1.0, 25, B)
+    pb.sync()
+    P = nodes.n_prog
+    assert torch.equal(A[:P], B[:P])
