@@ -337,6 +337,18 @@ int rbf_run(rbf_problem *pb, double t0, double dt, int64_t n_steps, void *U);
 int rbf_set_run_mode(rbf_problem *pb, int32_t mode, int32_t lanes, int32_t ctas);
 
 /*
+ * The node blocks of the persistent run mode, as a service for callers that
+ * want the same decomposition: recursive coordinate bisection of the n points
+ * (x, z) into `parts` blocks of equal size (+-1 node), each cut across the
+ * longer extent of the points being split, ties by index.
+ *   x, z      host, double [n]
+ *   block_of  host, int32 [n] (out): block of each point, 0 .. parts-1
+ * Host-only (no device call).  Errors: RBF_E_ARG for null pointers, n < 1,
+ * parts outside [1, n] or non-finite coordinates.
+ */
+int rbf_partition_blocks(const double *x, const double *z, int64_t n, int32_t parts, int32_t *block_of);
+
+/*
  * Bound on the polls of each grid-barrier wait of the persistent kernel
  * (default 2^21, about a second).  When a wait runs out, that CTA raises an
  * abort flag, every CTA leaves at its next barrier, the launch ends with the

@@ -1232,6 +1232,27 @@ void persistent_run_mlp(Problem &pb, double dt, int64_t n_steps, void *U, cudaSt
     ps.base += (unsigned)((uint64_t)ps.grid * (uint64_t)(4 * n_steps - 1));
 }
 
+}  // namespace rbf
+
+extern "C" int rbf_partition_blocks(const double *x, const double *z, int64_t n, int32_t parts, int32_t *block_of) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(x && z && block_of, "null argument");
+        RBF_REQUIRE(n >= 1 && n < ((int64_t)1 << 31), "n out of range");
+        RBF_REQUIRE(parts >= 1 && parts <= n, "parts must be in [1, n]");
+        std::vector<double> xs(x, x + n), zs(z, z + n);
+        for (int64_t k = 0; k < n; ++k)
+            RBF_REQUIRE(std::isfinite(xs[k]) && std::isfinite(zs[k]), "non-finite coordinate at %lld", (long long)k);
+        std::vector<int32_t> ids(n);
+        for (int64_t k = 0; k < n; ++k) ids[k] = (int32_t)k;
+        std::vector<std::pair<size_t, size_t>> blocks;
+        rbf::bisect(ids, 0, n, parts, xs, zs, blocks);
+        for (size_t b = 0; b < blocks.size(); ++b)
+            for (size_t k = blocks[b].first; k < blocks[b].second; ++k) block_of[ids[k]] = (int32_t)b;
+    });
+}
+
+namespace rbf {
+
 void persistent_check(Problem &pb) {
     if (pb.ps.abort.n == 0) return;
     int v = 0;

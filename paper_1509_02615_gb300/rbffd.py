@@ -97,6 +97,7 @@ SIGNATURES = [
     ("rbf_run_host", C.c_int, [_P, _D, _D, _I64, _P]),
     ("rbf_set_run_mode", C.c_int, [_P, _I32, _I32, _I32]),
     ("rbf_set_spin_limit", C.c_int, [_P, _I64]),
+    ("rbf_partition_blocks", C.c_int, [_P, _P, _I64, _I32, _P]),
     ("rbf_sync", C.c_int, [_P]),
     ("rbf_minmax", C.c_int, [_P, _P, _P]),
     ("rbf_get_info", C.c_int, [_P, C.POINTER(Info)]),
@@ -270,6 +271,16 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+def partition_blocks(x, z, parts):
+    """Block of every point under the persistent mode's recursive coordinate
+    bisection (host-only; see rbf_partition_blocks)."""
+    x = np.ascontiguousarray(x, np.float64)
+    z = np.ascontiguousarray(z, np.float64)
+    out = np.zeros(x.shape[0], np.int32)
+    _check(lib().rbf_partition_blocks(_host_ptr(x), _host_ptr(z), x.shape[0], int(parts), _host_ptr(out)))
+    return out
 
 
 def hyperviscosity_gamma(c, h, k):
