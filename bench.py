@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--threads-per-node", type=int, default=0, help="0 = autotuned")
+    ap.add_argument("--run-mode", default="auto", choices=["auto", "graph", "persistent"],
+                    help="headline run mode (auto: timed at creation); fixing it makes profiled runs reproducible")
+    ap.add_argument("--persistent-lanes", type=int, default=1, help="lanes per node with --run-mode persistent")
+    ap.add_argument("--persistent-ctas", type=int, default=0, help="CTAs with --run-mode persistent (0: one per SM)")
     ap.add_argument("--ens-runs", type=int, default=256, help="ensemble members (0 = skip the batched case)")
     ap.add_argument("--ens-steps", type=int, default=40, help="timed global RK4 steps of the ensemble")
     ap.add_argument("--learned", type=int, default=1, help="1 = measure the learned coarse-grid correction")
@@ -161,11 +165,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_problem(h, precision, tpn=0):
+def make_problem(h, precision, tpn=0, run_mode="auto", lanes=1, ctas=0):
     from paper_1509_02615_gb300 import inputs as inp
     from paper_1509_02615_gb300 import rbffd
     nodes = inp.density_current_nodes(h)
-    pb = rbffd.ns_problem(nodes, precision=precision, threads_per_node=tpn)
+    if run_mode == "auto":
+        pb = rbffd.ns_problem(nodes, precision=precision, threads_per_node=tpn)
+    else:
+        pb = rbffd.ns_problem(nodes, precision=precision, threads_per_node=tpn or 2)
+        pb.set_run_mode(run_mode, lanes=lanes if run_mode == "persistent" else 0, ctas=ctas)
     U0 = inp.density_current_state(nodes)
     return nodes, pb, U0
 
@@ -417,7 +425,8 @@ def main():
     torch.cuda.set_stream(stream)
     pk, pk_kind = peaks()
 
-    nodes, pb, U0 = make_problem(args.h, args.precision, args.threads_per_node)
+    nodes, pb, U0 = make_problem(args.h, args.precision, args.threads_per_node, args.run_mode,
+                                 args.persistent_lanes, args.persistent_ctas)
     info = pb.info()
     dt = args.h / 400.0
     U = rbffd.state_tensor(U0, args.precision)

@@ -130,6 +130,7 @@ void capture(Problem &pb, void *U, double dt, int steps) {
 
 void run(Problem &pb, double t0, double dt, int64_t n_steps, void *U) {
     RBF_REQUIRE(U != nullptr, "null state");
+    RBF_REQUIRE((reinterpret_cast<uintptr_t>(U) & 15) == 0, "state must be 16-byte aligned (node-major records)");
     RBF_REQUIRE(n_steps >= 0, "n_steps < 0");
     RBF_REQUIRE(std::isfinite(dt) && std::isfinite(t0), "non-finite time or step");
     if (n_steps == 0) return;
@@ -432,6 +433,8 @@ int rbf_adv_create(rbf_problem **out, const rbf_adv_params *prm, const double *x
 int rbf_rhs(rbf_problem *h, double t, void *U, void *dUdt) {
     return rbf::guarded([&] {
         RBF_REQUIRE(h && U && dUdt, "null argument");
+        RBF_REQUIRE(((reinterpret_cast<uintptr_t>(U) | reinterpret_cast<uintptr_t>(dUdt)) & 15) == 0,
+                    "state and tendency must be 16-byte aligned (node-major records)");
         RBF_REQUIRE(h->impl.kind != rbf::kEnsemble, "ensembles step with rbf_ens_run");
         rbf::enqueue_rhs(h->impl, t, U, dUdt, h->impl.st);
     });
@@ -440,6 +443,7 @@ int rbf_rhs(rbf_problem *h, double t, void *U, void *dUdt) {
 int rbf_rk4_step(rbf_problem *h, double t, double dt, void *U) {
     return rbf::guarded([&] {
         RBF_REQUIRE(h && U, "null argument");
+        RBF_REQUIRE((reinterpret_cast<uintptr_t>(U) & 15) == 0, "state must be 16-byte aligned (node-major records)");
         RBF_REQUIRE(std::isfinite(dt) && std::isfinite(t), "non-finite time or step");
         RBF_REQUIRE(h->impl.kind != rbf::kEnsemble, "ensembles step with rbf_ens_run");
         rbf::enqueue_rk4_step(h->impl, t, dt, U, h->impl.st, false, 0);

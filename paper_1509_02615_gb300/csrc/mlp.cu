@@ -725,6 +725,7 @@ int rbf_learned_run(rbf_mlp *h, double t0, double dt, int64_t n_steps, const dou
                     int64_t *n_fallback) {
     return rbf::guarded([&] {
         RBF_REQUIRE(h && U && alpha && n_steps >= 0, "bad argument");
+        RBF_REQUIRE((reinterpret_cast<uintptr_t>(U) & 15) == 0, "state must be 16-byte aligned (node-major records)");
         for (int f = 0; f < 4; ++f) RBF_REQUIRE(alpha[f] >= 0.0 && std::isfinite(alpha[f]), "alpha must be >= 0");
         const float4 al = make_float4((float)alpha[0], (float)alpha[1], (float)alpha[2], (float)alpha[3]);
         Mlp &m = h->impl;
@@ -826,6 +827,7 @@ int rbf_restrict_weighted(const void *src, int32_t src_precision, const int64_t 
 int rbf_fill_ghosts(rbf_problem *h, void *U) {
     return rbf::guarded([&] {
         RBF_REQUIRE(h && U && h->impl.kind == rbf::kNS, "needs a Navier-Stokes problem and a state");
+        RBF_REQUIRE((reinterpret_cast<uintptr_t>(U) & 15) == 0, "state must be 16-byte aligned (node-major records)");
         rbf::enqueue_ghost_fill(h->impl, U, h->impl.st);
     });
 }

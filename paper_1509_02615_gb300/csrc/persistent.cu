@@ -31,8 +31,8 @@
 // barrier.
 //
 // One stage per CTA: copy the listed records of the stage input into
-// shared memory (its own nodes' from registers, the others in one round of
-// independent L2 loads), solve its ghosts,
+// shared memory (its own nodes' from registers, the others by asynchronous
+// copies through L2, all in flight at once), solve its ghosts,
 // evaluate Eqs. (uEq)-(piEq) and the RK4 update for its nodes, write them,
 // and meet every other CTA at a grid barrier.  Every barrier wait is
 // bounded: after spin_limit polls a CTA raises the abort flag, every CTA
@@ -103,6 +103,24 @@ __device__ __forceinline__ void sh_store(float *S, int j, const Rec<float> &r) {
 __device__ __forceinline__ void sh_store(double *S, int j, const Rec<double> &r) {
     reinterpret_cast<double2 *>(S)[2 * j] = make_double2(r.u, r.w);
     reinterpret_cast<double2 *>(S)[2 * j + 1] = make_double2(r.t, r.p);
+}
+
+// Asynchronous 16-byte copies global -> shared through L2 (.cg: never a stale
+// L1 line), all in flight until cp_async_wait().
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+}
+// record j of U into record slot k of the shared list (one or two 16-byte copies)
+__device__ __forceinline__ void cp_rec(float *S, int k, const float *U, int64_t j) {
+    cp_async16(S + (size_t)k * 4, U + j * 4);
+}
+__device__ __forceinline__ void cp_rec(double *S, int k, const double *U, int64_t j) {
+    cp_async16(S + (size_t)k * 4, U + j * 4);
+    cp_async16(S + (size_t)k * 4 + 2, U + j * 4 + 2);
 }
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
@@ -411,7 +429,7 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
     {
         const int4 *src = reinterpret_cast<const int4 *>(a.blob + ci.blob_off);
         int4 *dst = reinterpret_cast<int4 *>(blob);
-        for (int k = threadIdx.x; k < ci.blob_bytes / 16; k += blockDim.x) dst[k] = __ldg(src + k);
+        for (int k = threadIdx.x; k < ci.blob_bytes / 16; k += blockDim.x) cp_async16(dst + k, src + k);
     }
     const uint16_t *ridx = reinterpret_cast<const uint16_t *>(blob);
     const T *rw = reinterpret_cast<const T *>(blob + ci.o_rw);
@@ -524,9 +542,9 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
             // registers (it wrote them), the others through L2 ----------------
             const bool first = step == 0 && st == 0;
             if (!first && live && g == 0) sh_store(halo, li, Rec<T>{o4[0], o4[1], o4[2], o4[3]});
-#pragma unroll 4
             for (int k = (first ? 0 : ci.n_own) + threadIdx.x; k < ci.n_load; k += blockDim.x)
-                sh_store(halo, k, ld_rec_cg(Uin, __ldg(hl + k)));
+                cp_rec(halo, k, Uin, __ldg(hl + k));
+            cp_async_wait();   // (at the first stage this also lands the constant block)
             __syncthreads();
             if (ci.n_rows > 0) {
                 // ---- residuals b - W_I u_I - W_B u_B of its wall rows -----------
