@@ -68,7 +68,7 @@ struct VecE<double> {
 // one ensemble member (same arithmetic and operand order as the single-problem
 // stage kernel with streamed operands).
 template <class T, int G, bool DIFF>
-__global__ void __launch_bounds__(256) ens_stage_kernel(const BlockDesc<T> *__restrict__ descs, EnsArgs<T> a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) ens_stage_kernel(const BlockDesc<T> *__restrict__ descs, EnsArgs<T> a) {
     using VT = VecE<T>;
     using W = typename VT::W;
     using I = typename VT::I;

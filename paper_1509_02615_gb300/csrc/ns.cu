@@ -75,7 +75,7 @@ constexpr int kPrefetchVec = 3;   // operand vectors per lane held in registers 
 // (constant data) are loaded into registers before grid_dep_wait(), so they
 // stream in while the preceding ghost kernels finish; PF == 0 streams them.
 template <class T, int G, bool DIFF, int PF>
-__global__ void __launch_bounds__(256) ns_stage_kernel(NSArgs<T> a) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && PF == 0) ? 4 : 1) ns_stage_kernel(NSArgs<T> a) {
     using VT = Vec<T>;
     using W = typename VT::W;
     using I = typename VT::I;
