@@ -96,14 +96,15 @@ def peaks():
 def kernel_source_hash(key=""):
     """Hash of the sources of the kernel a profile key names."""
     h = hashlib.sha256()
-    files = ("persistent.cu", "problem.cuh") if key.startswith("persistent") else ("ns.cu", "problem.cuh")
+    files = (("persistent.cu", "problem.cuh") if key.startswith("persistent") else
+             ("ensemble.cu", "problem.cuh") if key.startswith("ens_stage") else ("ns.cu", "problem.cuh"))
     for fn in files:
         with open(os.path.join(ROOT, "paper_1509_02615_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(key):
+def profiled_traffic(key, nodes=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -115,6 +116,8 @@ def profiled_traffic(key):
     e = d.get(key)
     if not e or e.get("source_hash") != kernel_source_hash(key):
         return None
+    if nodes is not None and "dram_bytes_per_node" in e:
+        return e["dram_bytes_per_node"] * nodes   # captured on a smaller launch of the same kernel
     return e.get("dram_bytes_per_launch")
 
 
@@ -274,7 +277,8 @@ def ensemble_case(torch, args):
            "timed_global_steps": K, "ms": ms, "node_updates_to_900s": ens.node_updates(-1),
            "threads_per_node": info["threads_per_node"],
            "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                        "frac": ach / pk["hbm_gbs"], "traffic": None, "kernel": "ens_stage_kernel",
+                        "frac": ach / pk["hbm_gbs"], "traffic": profiled_traffic("ens_stage_fp32", ens.n_prog),
+                        "kernel": "ens_stage_kernel",
                         "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg,
                         "peak_source": f"{pk_kind} hbm_gbs"},
            "setup": {"host_node_generation_s": t_gen, "gpu_build_ms": info["weight_build_ms"]},
