@@ -393,17 +393,37 @@ def cpu_baseline(h, budget_s=12.0):
 
 
 def run_reference(args, rank, world):
+    """The oracle arm: W untimed and K timed RK4 steps of the FP64 oracle on the
+    1/8-width strip of the workload (same spacing, stencils, walls), single
+    core; one step is four right-hand sides with their ghost solves."""
     if rank != 0:
         return
+    from oracle.ns import NSOracle
+    from paper_1509_02615_gb300 import inputs as inp
+    t_start = time.perf_counter()
+    width = 25600.0 / 8.0
+    nodes = inp.lattice_nodes("hex", -width, width, 0.0, 6400.0, args.h, True)
+    o = NSOracle(nodes)
+    dt = args.h / 400.0
+    U = inp.density_current_state(nodes)
+    for s in range(args.warmup):
+        U = o.rk4_step(s * dt, dt, U)
     t0 = time.perf_counter()
-    base = cpu_baseline(args.h, budget_s=max(5.0, min(60.0, 0.5 * args.steps)))
-    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "fp64 oracle", "l2": "n/a (CPU)"},
-            "cpu_baseline": base,
-            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": time.perf_counter() - t0}
+    for s in range(args.steps):
+        U = o.rk4_step((args.warmup + s) * dt, dt, U)
+    el = time.perf_counter() - t0
+    value = 4.0 * nodes.n_prog * args.steps / el
+    sample = (f"FP64 oracle RK4 steps (ghost solves + sparse DM products) on a periodic strip of the workload, 1/8 of "
+              f"its width ({nodes.n_prog} of 38400 nodes, same h, stencils and walls): {args.warmup} untimed + "
+              f"{args.steps} timed steps in {el:.2f} s, single-threaded scipy.sparse")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp64 oracle", "l2": "n/a (CPU)",
+                       "sample_nodes": nodes.n_prog},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_start}
     print(json.dumps(line), flush=True)
 
 
