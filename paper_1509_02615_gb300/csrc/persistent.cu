@@ -501,6 +501,9 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
     const int self = live ? li : 0;            // idle lanes mirror the first node
     const int64_t i = __ldg(hl + self);
 
+    // the first stage's records start moving before the operators do
+    for (int k = threadIdx.x; k < ci.n_load; k += blockDim.x) cp_rec(halo, k, a.U, __ldg(hl + k));
+
     const int64_t stride = a.lanes * G;        // in vectors, between consecutive q
     const int64_t off0 = ((int64_t)blockIdx.x * a.chunk + (li < a.chunk ? li : 0)) * G + g;
     const W *wx = reinterpret_cast<const W *>(a.pw);
@@ -542,9 +545,9 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
             // registers (it wrote them), the others through L2 ----------------
             const bool first = step == 0 && st == 0;
             if (!first && live && g == 0) sh_store(halo, li, Rec<T>{o4[0], o4[1], o4[2], o4[3]});
-            for (int k = (first ? 0 : ci.n_own) + threadIdx.x; k < ci.n_load; k += blockDim.x)
+            for (int k = (first ? ci.n_load : ci.n_own) + threadIdx.x; k < ci.n_load; k += blockDim.x)
                 cp_rec(halo, k, Uin, __ldg(hl + k));
-            cp_async_wait();   // (at the first stage this also lands the constant block)
+            cp_async_wait();   // (at the first stage: the constant block and the records issued at entry)
             __syncthreads();
             if (ci.n_rows > 0) {
                 // ---- residuals b - W_I u_I - W_B u_B of its wall rows -----------
