@@ -185,3 +185,49 @@ def front_location(nodes, theta, level=-0.5):
         return float(xs[i])
     t0, t1 = ts[i], ts[i + 1]
     return float(xs[i] + (level - t0) / (t1 - t0) * (xs[i + 1] - xs[i]))
+
+
+def facing_fronts(nodes, theta, x_mid, level=-0.5):
+    """Distances from x_mid to the nearest ground crossings of ``level`` on
+    either side (Sec. 6.3.2 table: the two fronts of the translating current
+    face each other about x = 18 km).  Returns (left, right) in metres, each by
+    linear interpolation between neighbouring ground nodes."""
+    g = np.nonzero(nodes.z[:nodes.n_prog] == nodes.domain[2])[0]
+    order = np.argsort(nodes.x[g])
+    xs, ts = nodes.x[g][order], theta[g][order]
+    cold = ts <= level
+    left = np.nonzero(cold & (xs < x_mid))[0]
+    right = np.nonzero(cold & (xs > x_mid))[0]
+    out = []
+    for idx, step in ((left, 1), (right, -1)):
+        if idx.size == 0:
+            out.append(float("nan"))
+            continue
+        i = idx[-1] if step == 1 else idx[0]
+        j = i + step                      # first warm node towards x_mid
+        t0, t1 = ts[i], ts[j]
+        xc = xs[i] + (level - t0) / (t1 - t0) * (xs[j] - xs[i])
+        out.append(float(abs(x_mid - xc)))
+    return tuple(out)
+
+
+def bubble_height(nodes, theta, x_line, level=0.1, dz=1.0):
+    """Height of the rising bubble (Sec. 6.4 table): the highest point of the
+    ``level`` contour on the vertical line x = x_line.  theta' is interpolated
+    to the line piecewise linearly on the Delaunay triangulation of the
+    prognostic nodes, sampled every dz metres, and the top crossing refined by
+    linear interpolation between samples."""
+    from scipy.interpolate import LinearNDInterpolator
+    n = nodes.n_prog
+    f = LinearNDInterpolator(np.c_[nodes.x[:n], nodes.z[:n]], theta[:n])
+    z0, z1 = nodes.domain[2], nodes.domain[3]
+    zs = np.arange(z0, z1 + 0.5 * dz, dz)
+    vals = f(np.full(zs.shape, x_line), zs)
+    vals = np.where(np.isnan(vals), -np.inf, vals)
+    above = np.nonzero(vals >= level)[0]
+    if above.size == 0:
+        return float("nan")
+    i = above[-1]
+    if i + 1 >= zs.shape[0]:
+        return float(zs[i])
+    return float(zs[i] + (vals[i] - level) / (vals[i] - vals[i + 1]) * dz)

@@ -12,6 +12,13 @@ closed-form, so no data set is involved).
                    walled [0, 20] x [0, 10] km box, Poisson-disk nodes at 25 m,
                    r^9 + deg 5, n = 56, Delta^3 from r^9, mu = 10,
                    dt = 1/16 s to 1000 s, FP64 weights in FP32
+  translating      Sec. 6.3.2: the density current in a periodic [0, 36] km
+                   domain carried by a 20 m/s background wind, r^7 + deg 4,
+                   n = 37, Delta^3, mu = 75, dt = h/400 to 900 s
+  rising_bubble    Sec. 6.4: C0 cone bubble (2 K, R = 1.5 km at (5, 3) km) in
+                   a walled [0, 10]^2 km box, Cartesian, hexagonal or
+                   scattered nodes, r^7 + deg 4, n = 37, Delta^3, mu = 10,
+                   dt = h/400 to 1100 s
   ensemble         256 density-current members (inputs.ensemble_members)
   learned          400 m coarse runs corrected by an MLP trained on fine runs
                    (learned.py)
@@ -56,3 +63,15 @@ def bubble(h: float = 25.0, seed: int = 1, t_end: float = 1000.0) -> Workload:
     nodes = inp.poisson_disk_nodes(0.0, 20000.0, 0.0, 10000.0, h, seed=seed)
     return Workload("bubble", nodes, dict(n=56, p=9, l=5, hv_k=3, hv_p=9, mu=10.0, gamma_c=BUBBLE_GAMMA_C),
                     inp.warm_bubble_state(nodes), h / 400.0, int(round(t_end * 400.0 / h)))
+
+
+def translating(h: float = 100.0, layout: str = "hex") -> Workload:
+    nodes = inp.translating_current_nodes(h, layout)
+    return Workload("translating", nodes, dict(n=37, p=7, l=4, hv_k=3, mu=75.0, gamma_c=2.0 ** -6),
+                    inp.translating_current_state(nodes), h / 400.0, int(round(900.0 * 400.0 / h)))
+
+
+def rising_bubble(h: float = 100.0, layout: str = "hex", seed: int = 1) -> Workload:
+    nodes = inp.rising_bubble_nodes(h, layout, seed=seed)
+    return Workload("rising_bubble", nodes, dict(n=37, p=7, l=4, hv_k=3, mu=10.0, gamma_c=2.0 ** -6),
+                    inp.cone_bubble_state(nodes), h / 400.0, int(round(1100.0 * 400.0 / h)))

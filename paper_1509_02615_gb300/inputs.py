@@ -151,6 +151,20 @@ def density_current_nodes(h: float = 100.0, layout: str = "hex", periodic_x: boo
     return lattice_nodes(layout, -25600.0, 25600.0, 0.0, 6400.0, h, periodic_x)
 
 
+def translating_current_nodes(h: float = 100.0, layout: str = "hex") -> NodeSet:
+    """Translating density-current domain [0, 36] x [0, 6.4] km, periodic in x
+    (Sec. 6.3.2, Wicker-Skamarock set-up)."""
+    return lattice_nodes(layout, 0.0, 36000.0, 0.0, 6400.0, h, periodic_x=True)
+
+
+def rising_bubble_nodes(h: float = 100.0, layout: str = "hex", seed: int = 1) -> NodeSet:
+    """Rising-bubble box [0, 10] x [0, 10] km with walls on all four sides
+    (Sec. 6.4): Cartesian or hexagonal lattice, or seeded Poisson-disk nodes."""
+    if layout == "scattered":
+        return poisson_disk_nodes(0.0, 10000.0, 0.0, 10000.0, h, seed=seed)
+    return lattice_nodes(layout, 0.0, 10000.0, 0.0, 10000.0, h, periodic_x=False)
+
+
 def unit_square_mirrored(m: int = 64, layers: int = 4) -> NodeSet:
     """Cartesian m x m nodes on [0,1]^2 (boundary nodes included, h = 1/(m-1))
     plus ``layers`` rows of nodes reflected across each wall and doubly
@@ -349,6 +363,28 @@ def warm_bubble_state(nodes: NodeSet, amp: float = 2.0, xc: float = 10000.0, zc:
     r = np.hypot(nodes.x - xc, nodes.z - zc)
     U = np.zeros((4, nodes.n_all))
     U[2] = np.where(r <= R, amp * np.cos(np.pi * r / (2.0 * R)) ** 2, 0.0)
+    U[:, nodes.n_prog:] = 0.0
+    return U
+
+
+def translating_current_state(nodes: NodeSet, ubar: float = 20.0, xc: float = 18000.0) -> np.ndarray:
+    """Translating density current (Sec. 6.3.2): the cold bubble of Sec. 6.3
+    centred at x = 18 km in the 36 km periodic domain, carried by a uniform
+    background wind ubar = 20 m/s held in u (a uniform u is a steady solution of
+    the unforced equations, so u keeps the full velocity).  After 900 s the
+    current has moved 18 km and its two fronts face each other about x = 18 km."""
+    U = density_current_state(nodes, xc=xc)
+    U[0, :nodes.n_prog] = ubar
+    return U
+
+
+def cone_bubble_state(nodes: NodeSet, amp: float = 2.0, xc: float = 5000.0, zc: float = 3000.0,
+                      R: float = 1500.0) -> np.ndarray:
+    """Rising thermal bubble of Sec. 6.4: the C0 cone theta' = amp max(0, 1 - r/R),
+    R = 1.5 km at (5, 3) km; u = w = pi' = 0."""
+    r = np.hypot(nodes.x - xc, nodes.z - zc)
+    U = np.zeros((4, nodes.n_all))
+    U[2] = amp * np.maximum(0.0, 1.0 - r / R)
     U[:, nodes.n_prog:] = 0.0
     return U
 
