@@ -176,6 +176,36 @@ int rbf_adv_create(rbf_problem **out, const rbf_adv_params *prm, const double *x
                    int64_t n_prog, int64_t n_all, const int32_t *src, const double *U,
                    const double *V, void *stream);
 
+/*
+ * One time-separable part of an advecting velocity: the flow is
+ * u(x, t) = sum_k c_k(t) U_k(x), v(x, t) = sum_k c_k(t) V_k(x) with
+ * c_k(t) = a + b cos(m pi t / T), T = rbf_adv_params.period_T.
+ */
+typedef struct rbf_flow_part {
+    double a, b, m;
+} rbf_flow_part;
+
+/*
+ * Flux-form advection (Sec. 6.1) in a velocity field made of n_parts (1 or 2)
+ * time-separable parts.  The vortex flow of Sec. 6.1,
+ * u = u_theta(r, t) sin(theta), v = -u_theta(r, t) cos(theta) with
+ * u_theta = (4 pi r / T) [1 - cos(2 pi t / T) (1 - (4r)^6) / (1 + (4r)^6)],
+ * is two parts: the solid-body rotation with c_1 = 1 ({1, 0, 0}) and the
+ * same rotation scaled by (1 - (4r)^6) / (1 + (4r)^6) with
+ * c_2 = -cos(2 pi t / T) ({0, -1, 2}).  rbf_adv_create is this call with one
+ * part {0, 1, 1}.
+ *   U, V    host, double [n_parts][n_all]: part k's spatial factors sampled
+ *           at every node's own position (reflected nodes included)
+ *   parts   host [n_parts]
+ * Other arguments, ownership and errors as rbf_adv_create; RBF_E_ARG for
+ * n_parts outside {1, 2} or a non-finite coefficient.  Each extra part adds
+ * one packed weight block (n_sten weights per node) to the stage kernel's
+ * stream.
+ */
+int rbf_adv_create_flow(rbf_problem **out, const rbf_adv_params *prm, const double *x, const double *z,
+                        int64_t n_prog, int64_t n_all, const int32_t *src, int32_t n_parts, const double *U,
+                        const double *V, const rbf_flow_part *parts, void *stream);
+
 /* One member of a batched ensemble (a8). */
 typedef struct rbf_ens_member {
     int64_t n_prog, n_all;  /* member's prognostic nodes and all nodes (ghosts last) */

@@ -368,9 +368,21 @@ int rbf_ns_create(rbf_problem **out, const rbf_ns_params *prm, const double *x, 
 
 int rbf_adv_create(rbf_problem **out, const rbf_adv_params *prm, const double *x, const double *z, int64_t n_prog,
                    int64_t n_all, const int32_t *src, const double *U, const double *V, void *stream) {
+    // the deformational flow: one part with c(t) = cos(pi t / T)
+    const rbf_flow_part part = {0.0, 1.0, 1.0};
+    return rbf_adv_create_flow(out, prm, x, z, n_prog, n_all, src, 1, U, V, &part, stream);
+}
+
+int rbf_adv_create_flow(rbf_problem **out, const rbf_adv_params *prm, const double *x, const double *z,
+                        int64_t n_prog, int64_t n_all, const int32_t *src, int32_t n_parts, const double *U,
+                        const double *V, const rbf_flow_part *parts, void *stream) {
     return rbf::guarded([&] {
-        RBF_REQUIRE(out && prm && src && U && V, "null argument");
+        RBF_REQUIRE(out && prm && src && U && V && parts, "null argument");
         *out = nullptr;
+        RBF_REQUIRE(n_parts == 1 || n_parts == 2, "n_parts must be 1 or 2, got %d", n_parts);
+        for (int k = 0; k < n_parts; ++k)
+            RBF_REQUIRE(std::isfinite(parts[k].a) && std::isfinite(parts[k].b) && std::isfinite(parts[k].m),
+                        "flow part %d has a non-finite coefficient", k);
         RBF_REQUIRE(prm->precision == 64 || prm->precision == 32, "precision must be 64 or 32");
         RBF_REQUIRE(prm->period_T > 0.0 && prm->gamma >= 0.0, "period_T must be > 0 and gamma >= 0");
         for (int64_t j = 0; j < n_all; ++j)
@@ -392,10 +404,20 @@ int rbf_adv_create(rbf_problem **out, const rbf_adv_params *prm, const double *x
             pb.hvc = prm->hv_k > 0 ? ((prm->hv_k % 2 == 1) ? 1.0 : -1.0) * prm->gamma : 0.0;
             pb.period_T = prm->period_T;
             pb.diff = 0;
-            pb.vel.alloc(2 * (size_t)n_all);
+            pb.n_vparts = n_parts;
+            for (int k = 0; k < n_parts; ++k) {
+                pb.vpart[k][0] = parts[k].a;
+                pb.vpart[k][1] = parts[k].b;
+                pb.vpart[k][2] = parts[k].m;
+            }
+            pb.vel.alloc(2 * (size_t)n_parts * n_all);
             pb.src.alloc(n_all);
-            RBF_CUDA(cudaMemcpyAsync(pb.vel.p, U, n_all * 8, cudaMemcpyHostToDevice, pb.st));
-            RBF_CUDA(cudaMemcpyAsync(pb.vel.p + n_all, V, n_all * 8, cudaMemcpyHostToDevice, pb.st));
+            for (int k = 0; k < n_parts; ++k) {
+                RBF_CUDA(cudaMemcpyAsync(pb.vel.p + (2 * k) * n_all, U + k * n_all, n_all * 8,
+                                         cudaMemcpyHostToDevice, pb.st));
+                RBF_CUDA(cudaMemcpyAsync(pb.vel.p + (2 * k + 1) * n_all, V + k * n_all, n_all * 8,
+                                         cudaMemcpyHostToDevice, pb.st));
+            }
             RBF_CUDA(cudaMemcpyAsync(pb.src.p, src, n_all * 4, cudaMemcpyHostToDevice, pb.st));
 
             cudaEvent_t e0, e1;
@@ -550,8 +572,11 @@ int rbf_get_info(const rbf_problem *h, rbf_info *out) {
             out->rhs_bytes_per_node = slots * (4 * ts + 4) + 4 * ts + 4 * ts + 8 * ts + 4 * ts + ts + 1;
             out->rhs_flops_per_node = slots * (12 * 2 + (pb.diff ? 4 : 0)) + 40 + 4 * 4;
         } else {
-            out->rhs_bytes_per_node = slots * (2 * ts + 4) + ts + ts + 2 * ts + ts;
-            out->rhs_flops_per_node = slots * 4 + 10;
+            // packed weights (velocity parts + hyperviscosity) + index per
+            // slot, the node's value, U_n, the accumulator read+write, the
+            // stage output
+            out->rhs_bytes_per_node = slots * ((pb.n_vparts + 1) * ts + 4) + ts + ts + 2 * ts + ts;
+            out->rhs_flops_per_node = slots * 2 * (pb.n_vparts + 1) + 10 + 4 * (pb.n_vparts - 1);
         }
     });
 }

@@ -182,20 +182,29 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && PF == 0) ? 4 : 1) ns_s
     }
 }
 
+// Velocity u(x, t) = sum_k c_k(t) (U_k, V_k)(x) with c_k(t) = fa_k + fb_k
+// cos(fm_k pi t / T): one separable part for the deformational flow, two for
+// the vortex flow of Sec. 6.1.  Packed block k holds part k's flux-form
+// weights; the hyperviscosity block follows the parts.
 template <class T>
 struct AdvArgs {
     const T *Uin, *Un;
     T *Uout, *K, *dUdt;
     const int32_t *pidx;
-    const T *wa, *wh;
+    const T *wa, *wa2, *wh;
     int64_t n_prog;
     int SL, stage;
     T a_next, b_stage;
     const double *tdev;   // device time (graph replays) or nullptr
     double t_host, t_frac_dt, period_T;
+    double fa[2], fb[2], fm[2];
 };
 
-template <class T, int G>
+__device__ __forceinline__ double flow_factor(double a, double b, double m, double t, double T) {
+    return b == 0.0 ? a : a + b * cos(m * 3.141592653589793 * t / T);
+}
+
+template <class T, int G, int NP>
 __global__ void __launch_bounds__(256) adv_stage_kernel(AdvArgs<T> a) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int g = (int)(tid % G);
@@ -204,7 +213,7 @@ __global__ void __launch_bounds__(256) adv_stage_kernel(AdvArgs<T> a) {
     if (!live) i = a.n_prog - 1;
     grid_dep_wait();
     grid_dep_launch();
-    T sa = 0, sh = 0;
+    T sa = 0, sb = 0, sh = 0;
     const int64_t stride = a.n_prog * G;
     int64_t off = i * G + g;
 #pragma unroll 4
@@ -212,18 +221,20 @@ __global__ void __launch_bounds__(256) adv_stage_kernel(AdvArgs<T> a) {
         const int j = __ldg(a.pidx + off);
         const T v = a.Uin[j];
         sa += __ldg(a.wa + off) * v;
+        if (NP == 2) sb += __ldg(a.wa2 + off) * v;
         sh += __ldg(a.wh + off) * v;
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
         sa += __shfl_xor_sync(0xffffffffu, sa, o, G);
+        if (NP == 2) sb += __shfl_xor_sync(0xffffffffu, sb, o, G);
         sh += __shfl_xor_sync(0xffffffffu, sh, o, G);
     }
     if (!live || g != 0) return;
-    // velocity time factor c(t) = cos(pi t / T) at this stage's time
+    // velocity time factors at this stage's time
     double t = (a.tdev ? *a.tdev : a.t_host) + a.t_frac_dt;
-    const T c = (T)cos(3.141592653589793 * t / a.period_T);
-    const T kf = c * sa + sh;
+    T kf = (T)flow_factor(a.fa[0], a.fb[0], a.fm[0], t, a.period_T) * sa + sh;
+    if (NP == 2) kf += (T)flow_factor(a.fa[1], a.fb[1], a.fm[1], t, a.period_T) * sb;
     if (a.stage < 0) {
         a.dUdt[i] = kf;
     } else {
@@ -278,14 +289,16 @@ __global__ void pack_kernel(const double *__restrict__ w64, const int32_t *__res
     }
 }
 
-// Advection: packed block 0 = flux-form weights -(Dx_ij U(x_j) + Dy_ij V(x_j)),
-// block 1 = (-1)^(k+1) gamma Delta^k weights; columns folded onto the source
-// node of reflected nodes (Sec. 6.1).  Weight blocks in w64: Dx, Dy, Delta^k.
+// Advection: packed block k < NP = flux-form weights of velocity part k,
+// -(Dx_ij U_k(x_j) + Dy_ij V_k(x_j)); block NP = (-1)^(k+1) gamma Delta^k
+// weights; columns folded onto the source node of reflected nodes
+// (Sec. 6.1).  Weight blocks in w64: Dx, Dy, Delta^k.  vel holds
+// [NP][U, V][n_all].
 template <class T>
 __global__ void pack_adv_kernel(const double *__restrict__ w64, const int32_t *__restrict__ idx, int64_t n_prog,
-                                int n, int has_hv, double hvc, const double *__restrict__ Uv,
-                                const double *__restrict__ Vv, const int32_t *__restrict__ src, int SL, int G,
-                                T *__restrict__ pw, int32_t *__restrict__ pidx) {
+                                int64_t n_all, int n, int has_hv, double hvc, const double *__restrict__ vel, int NP,
+                                const int32_t *__restrict__ src, int SL, int G, T *__restrict__ pw,
+                                int32_t *__restrict__ pidx) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t total = (int64_t)SL * G * n_prog;
     if (t >= total) return;
@@ -298,12 +311,12 @@ __global__ void pack_adv_kernel(const double *__restrict__ w64, const int32_t *_
         pidx[dst] = src[j];
         double dx = w64[((int64_t)0 * n_prog + i) * n + slot];
         double dy = w64[((int64_t)1 * n_prog + i) * n + slot];
-        pw[dst] = (T)(-(dx * Uv[j] + dy * Vv[j]));
-        pw[total + dst] = has_hv ? (T)(hvc * w64[((int64_t)2 * n_prog + i) * n + slot]) : (T)0;
+        for (int k = 0; k < NP; ++k)
+            pw[k * total + dst] = (T)(-(dx * vel[(2 * k) * n_all + j] + dy * vel[(2 * k + 1) * n_all + j]));
+        pw[NP * total + dst] = has_hv ? (T)(hvc * w64[((int64_t)2 * n_prog + i) * n + slot]) : (T)0;
     } else {
         pidx[dst] = (int32_t)i;
-        pw[dst] = (T)0;
-        pw[total + dst] = (T)0;
+        for (int k = 0; k <= NP; ++k) pw[k * total + dst] = (T)0;
     }
 }
 
@@ -358,16 +371,22 @@ void launch_ns(const NSArgs<T> &a, int G, int pf, cudaStream_t s, bool pdl) {
     }
 }
 
-template <class T>
-void launch_adv(const AdvArgs<T> &a, int G, cudaStream_t s, bool pdl) {
+template <class T, int NP>
+void launch_adv_np(const AdvArgs<T> &a, int G, cudaStream_t s, bool pdl) {
     const dim3 grid(div_up(a.n_prog * G, 256)), blk(256);
     switch (G) {
-        case 1: launch_kernel(adv_stage_kernel<T, 1>, grid, blk, s, pdl, a); break;
-        case 2: launch_kernel(adv_stage_kernel<T, 2>, grid, blk, s, pdl, a); break;
-        case 4: launch_kernel(adv_stage_kernel<T, 4>, grid, blk, s, pdl, a); break;
-        case 8: launch_kernel(adv_stage_kernel<T, 8>, grid, blk, s, pdl, a); break;
+        case 1: launch_kernel(adv_stage_kernel<T, 1, NP>, grid, blk, s, pdl, a); break;
+        case 2: launch_kernel(adv_stage_kernel<T, 2, NP>, grid, blk, s, pdl, a); break;
+        case 4: launch_kernel(adv_stage_kernel<T, 4, NP>, grid, blk, s, pdl, a); break;
+        case 8: launch_kernel(adv_stage_kernel<T, 8, NP>, grid, blk, s, pdl, a); break;
         default: RBF_FAIL(RBF_E_ARG, "threads per node %d not in {1,2,4,8}", G);
     }
+}
+
+template <class T>
+void launch_adv(const AdvArgs<T> &a, int G, cudaStream_t s, bool pdl) {
+    if (a.wa2) launch_adv_np<T, 2>(a, G, s, pdl);
+    else launch_adv_np<T, 1>(a, G, s, pdl);
 }
 
 template <class T>
@@ -400,10 +419,16 @@ AdvArgs<T> adv_args(Problem &pb) {
     const T *pw = (const T *)pb.pw.p;
     a.pidx = pb.pidx.p;
     a.wa = pw;
-    a.wh = pw + total;
+    a.wa2 = pb.n_vparts == 2 ? pw + total : nullptr;
+    a.wh = pw + pb.n_vparts * total;
     a.n_prog = pb.n_prog;
     a.SL = pb.SL;
     a.period_T = pb.period_T;
+    for (int k = 0; k < 2; ++k) {
+        a.fa[k] = pb.vpart[k][0];
+        a.fb[k] = pb.vpart[k][1];
+        a.fm[k] = pb.vpart[k][2];
+    }
     return a;
 }
 
@@ -471,17 +496,17 @@ void pack_operators(Problem &pb) {
     const int64_t total = (int64_t)pb.SL * pb.G * pb.n_prog;
     pb.pidx.alloc(total);
     if (pb.kind == kAdvection) {
-        pb.n_packed = 2;
-        pb.pw.alloc((size_t)2 * total * pb.tsize());
+        pb.n_packed = pb.n_vparts + 1;
+        pb.pw.alloc((size_t)pb.n_packed * total * pb.tsize());
         const int has_hv = nops > 2;
         if (pb.precision == 64)
             pack_adv_kernel<double><<<div_up(total, 256), 256, 0, pb.st>>>(
-                pb.w64.p, pb.idx.p, pb.n_prog, pb.n, has_hv, pb.hvc, pb.vel.p, pb.vel.p + pb.n_all, pb.src.p, pb.SL,
-                pb.G, (double *)pb.pw.p, pb.pidx.p);
+                pb.w64.p, pb.idx.p, pb.n_prog, pb.n_all, pb.n, has_hv, pb.hvc, pb.vel.p, pb.n_vparts, pb.src.p,
+                pb.SL, pb.G, (double *)pb.pw.p, pb.pidx.p);
         else
             pack_adv_kernel<float><<<div_up(total, 256), 256, 0, pb.st>>>(
-                pb.w64.p, pb.idx.p, pb.n_prog, pb.n, has_hv, pb.hvc, pb.vel.p, pb.vel.p + pb.n_all, pb.src.p, pb.SL,
-                pb.G, (float *)pb.pw.p, pb.pidx.p);
+                pb.w64.p, pb.idx.p, pb.n_prog, pb.n_all, pb.n, has_hv, pb.hvc, pb.vel.p, pb.n_vparts, pb.src.p,
+                pb.SL, pb.G, (float *)pb.pw.p, pb.pidx.p);
         RBF_CHECK_LAUNCH();
         RBF_CUDA(cudaStreamSynchronize(pb.st));
         return;

@@ -98,7 +98,9 @@ struct Problem {
     int p = 7, l = 4, hv_k = 0, hv_p = 7;
     // advection
     double period_T = 1.0;
-    DevBuf<double> vel;           // [2][n_all] spatial velocity factors U, V
+    int n_vparts = 1;             // separable velocity parts (1 or 2)
+    double vpart[2][3] = {{0.0, 1.0, 1.0}, {0.0, 0.0, 0.0}};   // c_k(t) = a + b cos(m pi t / T)
+    DevBuf<double> vel;           // [n_vparts][2][n_all] spatial velocity factors U_k, V_k
     DevBuf<int32_t> src;          // [n_all] source node of each node
 
     // FP64 setup products (kept for rbf_get_weights)

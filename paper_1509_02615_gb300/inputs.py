@@ -206,6 +206,64 @@ def unit_square_mirrored(m: int = 64, layers: int = 4) -> NodeSet:
                    h=h, layout="cart-mirror", domain=(0.0, 1.0, 0.0, 1.0))
 
 
+def unit_square_hex_mirrored(h: float = 0.005, layers: int = 5) -> NodeSet:
+    """Hexagonal lattice on [0,1]^2 with reflected layers (Sec. 6.1).
+
+    Rows are fitted to the height like the density-current lattice:
+    R = round(1 / (h sqrt(3)/2)) intervals of dy = 1/R; M = round(1/h) column
+    intervals of dx = 1/M; even rows hold x = c dx (c = 0..M, wall nodes
+    included), odd rows x = (c + 1/2) dx (c = 0..M-1).  The reflection of a
+    lattice node across any wall is a lattice node (row r -> -r or 2R - r keeps
+    its parity; an odd row's offsets map onto themselves), so the reflected
+    nodes continue the lattice: every lattice node within ``layers`` row or
+    column spacings outside the square is added, carrying the value of its
+    reflected source (corners reflected twice).
+    """
+    R = max(1, int(round(1.0 / (h * math.sqrt(3.0) / 2.0))))
+    M = max(1, int(round(1.0 / h)))
+    dx, dy = 1.0 / M, 1.0 / R
+
+    def row_cols(r, lo, hi):
+        # column numbers c of row r with lattice x in [lo*dx, hi*dx]
+        if r % 2 == 0:
+            return np.arange(lo, hi + 1)
+        return np.arange(lo, hi)   # x = (c + 1/2) dx
+
+    def xpos(r, c):
+        return (c + (0.5 if r % 2 else 0.0)) * dx
+
+    key = {}
+    xs, ys = [], []
+    for r in range(R + 1):
+        for c in row_cols(r, 0, M):
+            key[(r, int(c))] = len(xs)
+            xs.append(xpos(r, c))
+            ys.append(r * dy)
+    n_prog = len(xs)
+    mx, my, msrc = [], [], []
+    for r in range(-layers, R + layers + 1):
+        for c in row_cols(r, -layers, M + layers):
+            c = int(c)
+            inside_r = 0 <= r <= R
+            inside_c = (0 <= c <= M) if r % 2 == 0 else (0 <= c <= M - 1)
+            if inside_r and inside_c:
+                continue
+            sr = -r if r < 0 else (2 * R - r if r > R else r)
+            if r % 2 == 0:
+                sc = -c if c < 0 else (2 * M - c if c > M else c)
+            else:
+                sc = -c - 1 if c < 0 else (2 * M - c - 1 if c > M - 1 else c)
+            mx.append(xpos(r, c))
+            my.append(r * dy)
+            msrc.append(key[(sr, sc)])
+    x = np.concatenate([np.array(xs), np.array(mx)])
+    y = np.concatenate([np.array(ys), np.array(my)])
+    src = np.concatenate([np.arange(n_prog), np.array(msrc, np.int64)]).astype(np.int32)
+    return NodeSet(x=x, z=y, n_prog=n_prog, kind=np.zeros(n_prog, np.int32),
+                   ghost_owner=-np.ones(x.shape[0] - n_prog, np.int32), src=src, period_x=0.0,
+                   h=h, layout="hex-mirror", domain=(0.0, 1.0, 0.0, 1.0))
+
+
 def hilbert_order(x: np.ndarray, z: np.ndarray, bits: int = 16) -> np.ndarray:
     """Permutation sorting points along a Hilbert curve (locality for gathers)."""
     xs = (x - x.min()) / max(x.max() - x.min(), 1e-300)
@@ -403,6 +461,34 @@ def deformational_velocity(x, y):
     y = np.asarray(y)
     return (np.sin(np.pi * x) ** 2 * np.sin(2 * np.pi * y),
             -np.sin(np.pi * y) ** 2 * np.sin(2 * np.pi * x))
+
+
+def vortex_flow_parts(x, y, T=1.0):
+    """The vortex flow of Sec. 6.1 split into time-separable parts.
+
+    u_theta(r, t) = (4 pi r / T) [1 - cos(2 pi t / T) q(r)] with
+    q = (1 - (4r)^6) / (1 + (4r)^6), u = u_theta sin(theta),
+    v = -u_theta cos(theta), r sin(theta) = y - 1/2, r cos(theta) = x - 1/2
+    (theta taken in the quadrant of (x - 1/2, y - 1/2)).  Hence
+    (u, v) = c_1(t) (U_1, V_1) + c_2(t) (U_2, V_2) with the solid-body rotation
+    U_1 = 4 pi (y - 1/2) / T, V_1 = -4 pi (x - 1/2) / T, c_1 = 1, and
+    (U_2, V_2) = q (U_1, V_1), c_2 = -cos(2 pi t / T).
+    Returns ([(U_1, V_1), (U_2, V_2)], [(a, b, m)] per part) with
+    c_k(t) = a + b cos(m pi t / T)."""
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    r = np.hypot(x - 0.5, y - 0.5)
+    s6 = (4.0 * r) ** 6
+    q = (1.0 - s6) / (1.0 + s6)
+    U1 = 4.0 * np.pi * (y - 0.5) / T
+    V1 = -4.0 * np.pi * (x - 0.5) / T
+    return [(U1, V1), (q * U1, q * V1)], [(1.0, 0.0, 0.0), (0.0, -1.0, 2.0)]
+
+
+def vortex_bell(x, y):
+    """Initial scalar of the vortex-flow test (Sec. 6.1): the cosine bell
+    (1 + cos(pi rt))/2 with rt = 5 |(x, y) - (0.3, 0.5)|, i.e. radius 0.2."""
+    return cosine_bell(x, y, xc=0.3, yc=0.5, radius=0.2)
 
 
 def perturbed_density_current(nodes: NodeSet, seed: int) -> np.ndarray:

@@ -71,6 +71,8 @@ SIGNATURES = [
     ("rbf_build_weights", C.c_int, [_P, _P, _I64, _P, _I64, _I32, _D, _I32, _I32, _I32, _P, _I32, _P, _P]),
     ("rbf_ns_create", C.c_int, [C.POINTER(_P), C.POINTER(NSParams), _P, _P, _I64, _I64, _P, _P, _P]),
     ("rbf_adv_create", C.c_int, [C.POINTER(_P), C.POINTER(AdvParams), _P, _P, _I64, _I64, _P, _P, _P, _P]),
+    ("rbf_adv_create_flow", C.c_int, [C.POINTER(_P), C.POINTER(AdvParams), _P, _P, _I64, _I64, _P, _I32, _P, _P,
+                                      _P, _P]),
     ("rbf_ens_create", C.c_int, [C.POINTER(_P), C.POINTER(NSParams), _I32, C.POINTER(EnsMember), _P, _P, _P, _P,
                                  _P]),
     ("rbf_ens_run", C.c_int, [_P, _I64, _P]),
@@ -311,20 +313,33 @@ def ns_problem(nodes: inp.NodeSet, precision=64, n=37, p=7, l=4, hv_k=3, hv_p=No
 
 
 def advection_problem(nodes: inp.NodeSet, precision=64, n=37, p=7, l=4, hv_k=4, hv_p=9, gamma=None,
-                      gamma_c=2.0 ** -14, T=5.0):
-    """Scalar advection in the deformational flow on reflected nodes (Sec. 6.1)."""
+                      gamma_c=2.0 ** -14, T=5.0, flow="deformational"):
+    """Scalar advection on reflected nodes (Sec. 6.1) in the deformational
+    flow (one separable part, rbf_adv_create) or the paper's vortex flow (two
+    parts, rbf_adv_create_flow)."""
     prm = AdvParams(n_sten=n, phs_p=p, poly_l=l, hv_k=hv_k, hv_p=hv_p, precision=precision,
                     gamma=hyperviscosity_gamma(gamma_c, nodes.h, hv_k) if gamma is None else gamma, period_T=T)
     _torch()
-    Uv, Vv = inp.deformational_velocity(nodes.x, nodes.z)
-    Uv = np.ascontiguousarray(Uv, np.float64)
-    Vv = np.ascontiguousarray(Vv, np.float64)
     x = np.ascontiguousarray(nodes.x, np.float64)
     z = np.ascontiguousarray(nodes.z, np.float64)
     src = np.ascontiguousarray(nodes.src, np.int32)
     h = C.c_void_p()
-    _check(lib().rbf_adv_create(C.byref(h), C.byref(prm), _host_ptr(x), _host_ptr(z), nodes.n_prog, nodes.n_all,
-                                _host_ptr(src), _host_ptr(Uv), _host_ptr(Vv), _stream()))
+    if flow == "deformational":
+        Uv, Vv = inp.deformational_velocity(nodes.x, nodes.z)
+        Uv = np.ascontiguousarray(Uv, np.float64)
+        Vv = np.ascontiguousarray(Vv, np.float64)
+        _check(lib().rbf_adv_create(C.byref(h), C.byref(prm), _host_ptr(x), _host_ptr(z), nodes.n_prog, nodes.n_all,
+                                    _host_ptr(src), _host_ptr(Uv), _host_ptr(Vv), _stream()))
+    elif flow == "vortex":
+        parts, coef = inp.vortex_flow_parts(nodes.x, nodes.z, T)
+        Uv = np.ascontiguousarray(np.stack([pu for pu, _ in parts]), np.float64)
+        Vv = np.ascontiguousarray(np.stack([pv for _, pv in parts]), np.float64)
+        cf = np.ascontiguousarray(np.asarray(coef, np.float64).reshape(-1))
+        _check(lib().rbf_adv_create_flow(C.byref(h), C.byref(prm), _host_ptr(x), _host_ptr(z), nodes.n_prog,
+                                         nodes.n_all, _host_ptr(src), len(parts), _host_ptr(Uv), _host_ptr(Vv),
+                                         _host_ptr(cf), _stream()))
+    else:
+        raise ValueError(f"unknown flow {flow!r}")
     pb = Problem(h, 1, nodes.n_prog, nodes.n_all, precision, "advection")
     pb.params = prm
     return pb

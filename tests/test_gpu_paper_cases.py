@@ -1,0 +1,102 @@
+"""The paper's translating density current (Sec. 6.3.2) and rising thermal
+bubble (Sec. 6.4) on the GPU, through the C ABI.
+
+* Parity: 20 FP64 RK4 steps against the oracle at 800 m (translating,
+  periodic, background wind) and 400 m (bubble, walls on all sides, on all
+  three layouts), relative l2 < 1e-10 per field as in the other FP64 step
+  tests.
+* Printed tables.  Table translating: front distances from x = 18 km at
+  900 s, hexagonal 100 m and 50 m and Cartesian 100 m, FP64, within 60 m (the
+  bound of the Table straka check at 100 m).  Table bubble at 1100 s: 50 m in
+  FP64 on all three layouts and 25 m in FP32 (FP64-built weights) on the two
+  lattices; extrema of theta' within 0.05 K, of w within 0.25 m/s, bubble
+  height within 50 m (the bounds of the oracle's 200 m check).  The
+  scattered node set is this package's own seeded Poisson-disk draw.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle.ns import NSOracle, bubble_height, facing_fronts  # noqa: E402
+from paper_1509_02615_gb300 import configs  # noqa: E402
+from paper_1509_02615_gb300 import rbffd  # noqa: E402
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1509_02615_gb300 import _build
+    _build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+
+
+def _run(wl, precision, n_steps=None):
+    pb = rbffd.ns_problem(wl.nodes, precision=precision, **wl.params)
+    U = rbffd.state_tensor(wl.U0, precision)
+    pb.run(0.0, wl.dt, wl.n_steps if n_steps is None else n_steps, U)
+    pb.sync()
+    mm = pb.minmax(U)
+    got = rbffd.fields(U)
+    pb.close()
+    return got, mm
+
+
+@pytest.mark.parametrize("case", [("translating", 800.0, "hex"), ("rising_bubble", 400.0, "cart"),
+                                  ("rising_bubble", 400.0, "hex"), ("rising_bubble", 400.0, "scattered")])
+def test_fp64_steps_match_oracle(case):
+    name, h, layout = case
+    wl = getattr(configs, name)(h, layout)
+    ref = NSOracle(wl.nodes, **wl.params).run(wl.U0, 0.0, wl.dt, 20)
+    got, _ = _run(wl, 64, 20)
+    P = wl.nodes.n_prog
+    errs = [rel(got[f, :P], ref[f, :P]) for f in range(4)]
+    print(name, h, layout, "FP64 20 steps vs oracle:", [f"{e:.2e}" for e in errs])
+    assert max(errs) < 1e-10
+
+
+# Cartesian 50 m is left out: at dt = 1/8 s its largest |lambda dt| about the
+# 20 m/s wind is already 2.59 (RK4's imaginary-axis limit is 2.83), and the
+# ~50 m/s outflow winds of the resolved current push it past the limit.
+TRANSLATING_TABLE = {("cart", 100.0): (2487.0, 2512.0), ("hex", 100.0): (2555.0, 2580.0),
+                     ("hex", 50.0): (2595.0, 2595.0)}
+
+
+@pytest.mark.parametrize("key", list(TRANSLATING_TABLE))
+def test_translating_current_matches_paper_table(key):
+    layout, h = key
+    wl = configs.translating(h, layout)
+    got, _ = _run(wl, 64)
+    left, right = facing_fronts(wl.nodes, got[2], 18000.0)
+    ref = TRANSLATING_TABLE[key]
+    print("translating %s %g m FP64 at 900 s: fronts %.1f / %.1f m (paper %g / %g)" % (layout, h, left, right, *ref))
+    assert abs(left - ref[0]) < 60.0 and abs(right - ref[1]) < 60.0
+
+
+BUBBLE_TABLE = {          # min theta', max theta', min w, max w, height (Sec. 6.4 table)
+    ("cart", 50.0): (-0.02, 1.43, -7.87, 11.43, 8534.0),
+    ("hex", 50.0): (-0.02, 1.43, -7.75, 11.43, 8553.0),
+    ("scattered", 50.0): (-0.02, 1.43, -8.22, 11.43, 8525.0),
+    ("cart", 25.0): (0.00, 1.43, -7.74, 11.43, 8535.0),
+    ("hex", 25.0): (0.00, 1.43, -7.74, 11.43, 8535.0),
+}
+
+
+@pytest.mark.parametrize("key", list(BUBBLE_TABLE))
+def test_rising_bubble_matches_paper_table(key):
+    layout, h = key
+    wl = configs.rising_bubble(h, layout)
+    prec = 64 if h >= 50.0 else 32
+    got, mm = _run(wl, prec)
+    res = (mm[2, 0], mm[2, 1], mm[1, 0], mm[1, 1], bubble_height(wl.nodes, got[2], 5000.0))
+    ref = BUBBLE_TABLE[key]
+    print("bubble %s %g m FP%d at 1100 s:" % (layout, h, prec), np.round(res, 3), "paper", ref)
+    assert np.isfinite(res).all()
+    for a, b, tol in zip(res, ref, (0.05, 0.05, 0.25, 0.25, 50.0)):
+        assert abs(a - b) < tol, (res, ref)
