@@ -94,11 +94,12 @@ def peaks():
 
 
 def kernel_source_hash(key=""):
-    """Hash of the sources of the kernel a profile key names."""
+    """Hash of the source files holding the device code of the kernel a
+    profile key names: its translation unit and the device headers it uses."""
     h = hashlib.sha256()
-    files = (("persistent.cu", "problem.cuh") if key.startswith("persistent") else
-             ("ensemble.cu", "problem.cuh") if key.startswith("ens_stage") else ("ns.cu", "problem.cuh"))
-    for fn in files:
+    unit = ("persistent.cu" if key.startswith("persistent") else
+            "ensemble.cu" if key.startswith("ens_stage") else "ns.cu")
+    for fn in (unit, "records.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_1509_02615_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -232,6 +233,35 @@ def large_case(torch, args, flush):
                         "peak_source": f"{pk_kind} hbm_gbs"},
            "threads_per_node": info["threads_per_node"], "prefetch": info["prefetch"],
            "setup": {"weight_build_ms": info["weight_build_ms"], "ghost_setup_ms": info["ghost_setup_ms"]}}
+    # f4: the same steps with lattice operator storage (one operator row per
+    # class of translated stencils); its bytes per node-RHS follow the storage
+    Ur = U.clone()
+    t0 = time.perf_counter()
+    cn, nc = pb.set_operator_storage("lattice")
+    lat_setup_s = time.perf_counter() - t0
+    li = pb.info()
+    Ul = rbffd.state_tensor(U0, 32)
+    lstep, _ = time_steps(torch, pb, Ul, dt, steps, 3, flush, False)
+    _, lstage = time_steps(torch, pb, Ul, dt, steps, 1, flush, True)
+    lavg = float(np.mean(lstage)) / 4.0
+    lbpl = li["rhs_bytes_per_node"] * nodes.n_prog
+    lach = lbpl / (lavg / 1e3) / 1e9
+    # same number of steps from the same state as the per-node run above
+    fl, fp = rbffd.fields(Ul)[:, :nodes.n_prog], rbffd.fields(Ur)[:, :nodes.n_prog]
+    out["lattice"] = {
+        "node_rhs_per_s": 4.0 * nodes.n_prog * steps / (float(sum(lstep)) / 1e3),
+        "ms_per_step": float(sum(lstep)) / steps, "avg_stage_kernel_ms": lavg,
+        "speedup_vs_per_node": float(sum(step_ms)) / float(sum(lstep)),
+        "classes": nc, "class_nodes": cn, "class_fraction": cn / nodes.n_prog,
+        "rhs_bytes_per_node": li["rhs_bytes_per_node"], "threads_per_node": li["threads_per_node"],
+        "roofline": {"bound": "hbm", "achieved": lach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": lach / pk["hbm_gbs"], "traffic": profiled_traffic(f"ns_stage_lattice_fp32_hex{int(args.large_h)}"),
+                     "algorithmic_bytes_per_launch": lbpl, "avg_launch_ms": lavg,
+                     "peak_source": f"{pk_kind} hbm_gbs",
+                     "note": "algorithmic bytes of the lattice storage: class id + records, no per-node operators"},
+        "rel_l2_vs_per_node_after_%d_steps" % (2 * steps + 4): [
+            float(np.linalg.norm(fl[f] - fp[f]) / max(np.linalg.norm(fp[f]), 1e-30)) for f in range(4)],
+        "setup_s": lat_setup_s}
     pb.close()
     return out
 
@@ -370,26 +400,63 @@ def learned_case(torch, args):
     return out
 
 
-def cpu_baseline(h, budget_s=12.0):
-    """FP64 oracle on a 1/8-width periodic strip of the same workload (same
-    spacing, stencils, operators and boundary treatment): node-RHS/s."""
+def _oracle_strip(h):
+    """The FP64 oracle on a 1/8-width periodic strip of the workload (same
+    spacing, stencils, operators and boundary treatment), its setup time
+    (stencils, weights, ghost factorisations) and a state one step in."""
     from oracle.ns import NSOracle
     from paper_1509_02615_gb300 import inputs as inp
     width = 25600.0 / 8.0
     nodes = inp.lattice_nodes("hex", -width, width, 0.0, 6400.0, h, True)
+    t0 = time.perf_counter()
     o = NSOracle(nodes)
+    setup_s = time.perf_counter() - t0
     U = inp.density_current_state(nodes)
     U = o.rk4_step(0.0, h / 400.0, U)
+    return nodes, o, U, setup_s
+
+
+def _oracle_rhs_rate(args):
+    """RHS evaluations of one strip for budget_s seconds: (evaluations,
+    nodes, seconds, setup seconds).  Runs in a spawned worker process."""
+    h, budget_s = args
+    nodes, o, U, setup_s = _oracle_strip(h)
     t0 = time.perf_counter()
     n_eval = 0
     while time.perf_counter() - t0 < budget_s:
         o.rhs(0.0, U)
         n_eval += 1
-    el = time.perf_counter() - t0
-    return {"value": n_eval * nodes.n_prog / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 oracle RHS (ghost solve + sparse DM products) on a periodic strip of the "
-                      f"workload, 1/8 of its width ({nodes.n_prog} of 38400 nodes, same h, stencils and walls), {n_eval} evaluations "
-                      f"in {el:.1f} s, single-threaded scipy.sparse"}
+    return n_eval, nodes.n_prog, time.perf_counter() - t0, setup_s
+
+
+def cpu_baseline(h, budget_s=12.0):
+    """FP64 oracle node-RHS/s on the host cores: one strip per core in spawned
+    single-threaded processes (the headline figure), and one core alone."""
+    import multiprocessing as mp
+    n_eval, n_prog, el, setup_s = _oracle_rhs_rate((h, budget_s))
+    single = n_eval * n_prog / el
+    cores = os.cpu_count() or 1
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"          # the spawned workers' BLAS stays single-threaded
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_rhs_rate, [(h, budget_s)] * cores)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    value = sum(ne * npg / t for ne, npg, t, _ in res)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle RHS (ghost solve + sparse DM products) on periodic strips of the workload, 1/8 of "
+                      f"its width ({n_prog} of 38400 nodes, same h, stencils and walls): one strip per core in "
+                      f"{cores} spawned single-threaded processes, {sum(r[0] for r in res)} evaluations in "
+                      f"{budget_s:.0f} s each",
+            "single_core": {"value": single, "cores": 1, "evaluations": n_eval, "seconds": el},
+            "oracle_setup_s": setup_s}
 
 
 def run_reference(args, rank, world):
@@ -543,6 +610,22 @@ def main():
                              "hbm_GBps": i64["rhs_bytes_per_node"] * n64.n_prog / (avg64 / 1e3) / 1e9},
                 "threads_per_node": i64["threads_per_node"],
                 "run_mode": "persistent" if i64["run_mode"] == 2 else "graph"}
+        # accuracy of the FP32 form: the whole run to 900 s in both precisions
+        # (the FP64 path matches the FP64 oracle to ~1e-12), per-field
+        # relative l2 of FP32 against FP64 at t_final
+        n_end = int(round(900.0 / dt))
+        A64 = rbffd.state_tensor(U0, 64)
+        pb64.run(0.0, dt, n_end, A64)
+        pb64.sync()
+        A32 = rbffd.state_tensor(U0, 32)
+        pb.run(0.0, dt, n_end, A32)
+        pb.sync()
+        f64 = rbffd.fields(A64)[:, :nodes.n_prog]
+        f32 = rbffd.fields(A32)[:, :nodes.n_prog]
+        fp64["fp32_error_at_900s"] = {
+            "fields": ["u", "w", "theta'", "pi'"],
+            "rel_l2_vs_fp64": [float(np.linalg.norm(f32[f] - f64[f]) / np.linalg.norm(f64[f])) for f in range(4)],
+            "steps": n_end}
         pb64.close()
 
     large = None

@@ -378,6 +378,47 @@ int rbf_set_run_mode(rbf_problem *pb, int32_t mode, int32_t lanes, int32_t ctas)
  */
 int rbf_partition_blocks(const double *x, const double *z, int64_t n, int32_t parts, int32_t *block_of);
 
+/* Operator storage of the stage kernels (rbf_set_operator_storage). */
+#define RBF_STORE_PER_NODE 0
+#define RBF_STORE_LATTICE 1
+
+/*
+ * f4 (beyond the paper): how the graph-mode stage kernels store their
+ * operators.  RBF_STORE_PER_NODE (the default) keeps one packed row of every
+ * differentiation matrix per node, as Sec. 3 builds them.  RBF_STORE_LATTICE
+ * groups nodes whose stencils are translates of each other -- the same
+ * relative index offsets and relative positions, as on the interior and the
+ * wall rows of Cartesian and hexagonal lattices -- into classes of at least
+ * 32 members.  Each class keeps the packed operators of its first member,
+ * and the stage kernel reads them from a table of a few tens of kB; the
+ * other nodes keep their own rows.  The weights of a class's members agree
+ * with its first member's up to rounding (identical augmented systems of
+ * Eq. (weights)).  threads_per_node: 0 re-runs the autotuner with the new
+ * storage, else 1, 2, 4 or 8.  class_nodes, n_classes (nullable, host)
+ * receive the number of nodes in classes and of classes (0 for per-node
+ * storage).  rbf_get_info's rhs_bytes_per_node follows the storage.  The
+ * persistent run mode keeps its own operators and is not affected.
+ * Synchronises the problem's stream.  RBF_E_ARG for an advection problem or
+ * an unknown mode.
+ */
+int rbf_set_operator_storage(rbf_problem *pb, int32_t mode, int32_t threads_per_node, int64_t *class_nodes,
+                             int32_t *n_classes);
+
+/*
+ * Host-only: the lattice classes of rbf_set_operator_storage for given
+ * stencils.  idx [n_prog][n_sten] (host, int32, indices into the n_all
+ * nodes), x, z [n_all] (host); period_x > 0 for a periodic x; h is the unit
+ * of the position keys (relative positions are compared at h / 2^20).
+ * cls [n_prog] (host) receives each node's class in the order of the
+ * classes' first members, or -1 for nodes whose class has fewer than
+ * min_members members; *n_classes the number of classes.  RBF_E_ARG for
+ * null pointers, indices outside [0, n_all), non-finite coordinates or
+ * h <= 0.
+ */
+int rbf_lattice_classes(const int32_t *idx, const double *x, const double *z, int64_t n_prog, int64_t n_all,
+                        int32_t n_sten, double period_x, double h, int32_t min_members, int32_t *cls,
+                        int32_t *n_classes);
+
 /*
  * Bound on the polls of each grid-barrier wait of the persistent kernel
  * (default 2^21, about a second).  When a wait runs out, that CTA raises an

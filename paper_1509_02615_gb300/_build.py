@@ -8,7 +8,7 @@ import subprocess
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-SOURCES = ["stencils.cu", "weights.cu", "ghost.cu", "ns.cu", "persistent.cu", "ensemble.cu", "mlp.cu", "api.cu"]
+SOURCES = ["stencils.cu", "weights.cu", "ghost.cu", "ns.cu", "persistent.cu", "ensemble.cu", "mlp.cu", "lattice.cu", "api.cu"]
 LIB = os.path.join(PKG, "librbffd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]

@@ -91,7 +91,8 @@ void choose_threads(Problem &pb, int requested) {
                     "threads_per_node must be 0, 1, 2, 4 or 8");
         pb.G = requested;
         pack_operators(pb);
-        pb.pf = (pb.kind == kNS && pb.SLQ <= 3) ? 3 : 0;   // registers hold the operands when they fit
+        // registers hold the operands when they fit (per-node storage only)
+        pb.pf = (pb.kind == kNS && pb.SLQ <= 3 && !pb.lat.enabled) ? 3 : 0;
     }
 }
 
@@ -515,6 +516,27 @@ int rbf_set_run_mode(rbf_problem *h, int32_t mode, int32_t lanes, int32_t ctas) 
     });
 }
 
+int rbf_set_operator_storage(rbf_problem *h, int32_t mode, int32_t threads_per_node, int64_t *class_nodes,
+                             int32_t *n_classes) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h, "null problem");
+        Problem &pb = h->impl;
+        RBF_REQUIRE(pb.kind == rbf::kNS, "operator storage applies to Navier-Stokes problems");
+        RBF_REQUIRE(mode == RBF_STORE_PER_NODE || mode == RBF_STORE_LATTICE, "unknown storage mode %d", mode);
+        RBF_REQUIRE(threads_per_node == 0 || threads_per_node == 1 || threads_per_node == 2 ||
+                        threads_per_node == 4 || threads_per_node == 8,
+                    "threads_per_node must be 0, 1, 2, 4 or 8");
+        RBF_CUDA(cudaStreamSynchronize(pb.st));
+        RBF_CUDA(cudaStreamSynchronize(pb.cap));
+        rbf::invalidate_graph(pb);
+        pb.lat.enabled = mode == RBF_STORE_LATTICE;
+        if (threads_per_node == 0) RBF_REQUIRE(pb.S0.p, "autotuning needs the stage buffers");
+        rbf::choose_threads(pb, threads_per_node);
+        if (class_nodes) *class_nodes = pb.lat.enabled ? pb.lat.class_nodes : 0;
+        if (n_classes) *n_classes = pb.lat.enabled ? pb.lat.n_cls : 0;
+    });
+}
+
 int rbf_set_spin_limit(rbf_problem *h, int64_t polls) {
     return rbf::guarded([&] {
         RBF_REQUIRE(h, "null problem");
@@ -570,6 +592,14 @@ int rbf_get_info(const rbf_problem *h, rbf_info *out) {
             // values, U_n, the RK4 accumulator read+write, the stage output,
             // pibar and the flag byte
             out->rhs_bytes_per_node = slots * (4 * ts + 4) + 4 * ts + 4 * ts + 8 * ts + 4 * ts + ts + 1;
+            if (pb.lat.enabled && pb.kind == rbf::kNS) {
+                // lattice storage: class nodes read a class id instead of their
+                // operators; irregular nodes read both; the class table once
+                const double cn = (double)pb.lat.class_nodes, N = (double)pb.n_prog;
+                const double table = (double)pb.lat.n_cls * pb.SLQ * pb.G * pb.V * (4 * ts + 4);
+                out->rhs_bytes_per_node = 4 + (4 * ts + 4 * ts + 8 * ts + 4 * ts + ts + 1) +
+                                          (N - cn) / N * slots * (4 * ts + 4) + table / N;
+            }
             out->rhs_flops_per_node = slots * (12 * 2 + (pb.diff ? 4 : 0)) + 40 + 4 * 4;
         } else {
             // packed weights (velocity parts + hyperviscosity) + index per

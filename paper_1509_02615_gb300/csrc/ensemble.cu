@@ -329,6 +329,7 @@ void merge_ghosts(Problem &pb) {
     RBF_CUDA(cudaMemcpy(M.grec.p, grec.data(), ng * 8, cudaMemcpyHostToDevice));
     RBF_CUDA(cudaMemcpy(M.comp_start.p, cstart.data(), (nc + 1) * 8, cudaMemcpyHostToDevice));
     RBF_CUDA(cudaMemcpy(M.inv_off.p, inv_off.data(), inv_off.size() * 8, cudaMemcpyHostToDevice));
+    build_ghost_bands(M, sizeof(T) == 8 ? 64 : 32, pb.st);
     // the members' own ghost plans are no longer needed
     for (auto &m : E.members) m->gh = GhostPlan();
 }

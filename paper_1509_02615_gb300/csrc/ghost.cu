@@ -10,9 +10,12 @@
 // one launch pair per pivot, all blocks batched).
 // Every RK stage: (1) one thread per (field, wall row) forms the residual
 // r = b - W_I u_I - W_B u_B from the row's stencil; (2) one warp per
-// (field, ghost) forms u_G = W_G^{-1} r as a dense dot product within its
-// component.  Both kernels are tiny next to the right-hand side; the dense
-// inverse trades a few MB of L2-resident reads for a fully parallel solve.
+// (class, ghost) forms u_G = W_G^{-1} r from the banded inverse row.  The
+// rows of W_G^{-1} decay geometrically along the wall (the wall rows couple
+// only nearby ghosts), so each row keeps the entries above 2^-8 eps of its
+// largest (eps of the run's precision): the dropped tail is below the
+// rounding of the kept sum, and a row reads ~50-100 entries instead of the
+// whole component.
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -123,7 +126,6 @@ __global__ void to_t(const double *src, T *dst, int64_t n) {
 
 constexpr int kRowLanes = 8;    // lanes per wall row in the residual kernel
 constexpr int kRowPf = 16;      // slots per lane held in registers
-constexpr int kInvPf = 16;      // inverse entries per lane held in registers
 
 // r[f][pos(r)] = b_f(r) - sum over the row's non-ghost stencil nodes, all four
 // fields at once from one record gather per slot; 8 lanes per row share the
@@ -186,51 +188,48 @@ __global__ void __launch_bounds__(256) ghost_residual(const T *__restrict__ U, i
     res[ln * ng + pos[r]] = b - acc;
 }
 
-// u_G = W_G^{-1} r within each component: one warp per (class, position)
-// computes every field of that boundary-operator class from one pass over
-// the inverse row (held in registers before the wait).  grec[q] is the state
-// record of the ghost at position q; rows <= ng positions are processed.
+// u_G = W_G^{-1} r within each component, one warp per (class, position)
+// computing every field of that boundary-operator class.  The kept entries
+// of row (class, q) are bval[brow[r] .. brow[r+1]) at positions bcol
+// (absolute, within the component), r = class * ng + q; the first
+// kBandPf * 32 entries of a row are loaded before the wait.
+constexpr int kBandPf = 4;
+
 template <class T>
-__global__ void __launch_bounds__(256) ghost_apply(T *__restrict__ U, int64_t ng, int64_t rows,
-                                                   const int32_t *__restrict__ comp_of,
-                                                   const int64_t *__restrict__ comp_start,
-                                                   const int64_t *__restrict__ inv_off, int n_comp, int n_class,
-                                                   const T *__restrict__ inv, const T *__restrict__ res,
-                                                   const int64_t *__restrict__ grec, int4 cls_fields) {
+__global__ void __launch_bounds__(256) ghost_apply_band(T *__restrict__ U, int64_t ng, int64_t rows, int n_class,
+                                                        const int64_t *__restrict__ brow,
+                                                        const int32_t *__restrict__ bcol,
+                                                        const T *__restrict__ bval, const T *__restrict__ res,
+                                                        const int64_t *__restrict__ grec, int4 cls_fields) {
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     const bool live = wid < (int64_t)n_class * rows;
     const int64_t w = live ? wid : 0;
     const int cls = (int)(w / rows);
     const int64_t q = w - (int64_t)cls * rows;
-    const int c = comp_of[q];
-    const int64_t s0 = comp_start[c];
-    const int m = (int)(comp_start[c + 1] - s0);
-    const int row = (int)(q - s0);
-    const T *Ainv = inv + inv_off[cls * n_comp + c] + (int64_t)row * m;
-    T a[kInvPf];
+    const int64_t r = (int64_t)cls * ng + q;
+    const int64_t b0 = __ldg(brow + r), b1 = __ldg(brow + r + 1);
+    T a[kBandPf];
+    int col[kBandPf];
 #pragma unroll
-    for (int t = 0; t < kInvPf; ++t) a[t] = (lane + 32 * t < m) ? __ldg(Ainv + lane + 32 * t) : (T)0;
+    for (int t = 0; t < kBandPf; ++t) {
+        const int64_t e = b0 + lane + 32 * t;
+        const bool in = e < b1;
+        a[t] = in ? __ldg(bval + e) : (T)0;
+        col[t] = in ? __ldg(bcol + e) : 0;
+    }
     const int fm = cls == 0 ? cls_fields.x : cls == 1 ? cls_fields.y : cls == 2 ? cls_fields.z : cls_fields.w;
     grid_dep_wait();
     grid_dep_launch();
     if (!live) return;
-    T acc[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         if (!(fm & (1 << f))) continue;
-        const T *rr = res + f * ng + s0;
+        const T *rr = res + f * ng;
         T s = 0;
 #pragma unroll
-        for (int t = 0; t < kInvPf; ++t)
-            if (lane + 32 * t < m) s += a[t] * rr[lane + 32 * t];
-        for (int j = lane + 32 * kInvPf; j < m; j += 32) s += __ldg(Ainv + j) * rr[j];
-        acc[f] = s;
-    }
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        if (!(fm & (1 << f))) continue;
-        T s = acc[f];
+        for (int t = 0; t < kBandPf; ++t) s += a[t] * rr[col[t]];
+        for (int64_t e = b0 + lane + 32 * kBandPf; e < b1; e += 32) s += __ldg(bval + e) * rr[__ldg(bcol + e)];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) U[grec[q] * 4 + f] = s;
     }
@@ -467,11 +466,71 @@ void build_ghost_plan(Problem &pb, const int32_t *kind_host, const int32_t *owne
     RBF_CUDA(cudaMemcpyAsync(gh.comp_of.p, comp_of.data(), ng * 4, cudaMemcpyHostToDevice, st));
     RBF_CUDA(cudaMemcpyAsync(gh.comp_start.p, cstart.data(), (nc + 1) * 8, cudaMemcpyHostToDevice, st));
     RBF_CUDA(cudaMemcpyAsync(gh.inv_off.p, moff.data(), nm * 8, cudaMemcpyHostToDevice, st));
+    build_ghost_bands(gh, pb.precision, st);
     RBF_CUDA(cudaEventRecord(e1, st));
     RBF_CUDA(cudaStreamSynchronize(st));
     RBF_CUDA(cudaEventElapsedTime(&pb.ghost_setup_ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+}
+
+void build_ghost_bands(GhostPlan &gh, int precision, cudaStream_t st) {
+    const int64_t ng = gh.n_ghost;
+    if (ng == 0) return;
+    const size_t ts = precision == 64 ? 8 : 4;
+    std::vector<int32_t> comp_of(ng);
+    std::vector<int64_t> cstart(gh.n_comp + 1), ioff((size_t)gh.n_class * gh.n_comp);
+    std::vector<unsigned char> inv(gh.inv.bytes());
+    RBF_CUDA(cudaMemcpyAsync(comp_of.data(), gh.comp_of.p, ng * 4, cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(cudaMemcpyAsync(cstart.data(), gh.comp_start.p, cstart.size() * 8, cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(cudaMemcpyAsync(ioff.data(), gh.inv_off.p, ioff.size() * 8, cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(cudaMemcpyAsync(inv.data(), gh.inv.p, inv.size(), cudaMemcpyDeviceToHost, st));
+    RBF_CUDA(cudaStreamSynchronize(st));
+    auto inv_at = [&](int64_t e) {
+        if (precision == 64) {
+            double v;
+            memcpy(&v, inv.data() + e * 8, 8);
+            return v;
+        }
+        float v;
+        memcpy(&v, inv.data() + e * 4, 4);
+        return (double)v;
+    };
+    const double thr = std::ldexp(precision == 64 ? 2.220446049250313e-16 : 1.1920928955078125e-07, -8);
+    std::vector<int64_t> brow((size_t)gh.n_class * ng + 1, 0);
+    std::vector<int32_t> bcol;
+    std::vector<double> bval;
+    for (int cl = 0; cl < gh.n_class; ++cl)
+        for (int64_t q = 0; q < ng; ++q) {
+            const int c = comp_of[q];
+            const int64_t s0 = cstart[c];
+            const int64_t m = cstart[c + 1] - s0;
+            const int64_t row0 = ioff[(size_t)cl * gh.n_comp + c] + (q - s0) * m;
+            double mx = 0.0;
+            for (int64_t j = 0; j < m; ++j) mx = std::max(mx, std::fabs(inv_at(row0 + j)));
+            for (int64_t j = 0; j < m; ++j) {
+                const double v = inv_at(row0 + j);
+                if (v != 0.0 && std::fabs(v) >= thr * mx) {
+                    bcol.push_back((int32_t)(s0 + j));
+                    bval.push_back(v);
+                }
+            }
+            brow[(size_t)cl * ng + q + 1] = (int64_t)bcol.size();
+        }
+    gh.band_nnz = (int64_t)bcol.size();
+    gh.brow.alloc(brow.size());
+    gh.bcol.alloc(std::max<size_t>(bcol.size(), 1));
+    gh.bval.alloc(std::max<size_t>(bval.size(), 1) * ts);
+    RBF_CUDA(cudaMemcpyAsync(gh.brow.p, brow.data(), brow.size() * 8, cudaMemcpyHostToDevice, st));
+    RBF_CUDA(cudaMemcpyAsync(gh.bcol.p, bcol.data(), bcol.size() * 4, cudaMemcpyHostToDevice, st));
+    if (precision == 64) {
+        RBF_CUDA(cudaMemcpyAsync(gh.bval.p, bval.data(), bval.size() * 8, cudaMemcpyHostToDevice, st));
+        RBF_CUDA(cudaStreamSynchronize(st));
+    } else {
+        std::vector<float> bf(bval.begin(), bval.end());
+        RBF_CUDA(cudaMemcpyAsync(gh.bval.p, bf.data(), bf.size() * 4, cudaMemcpyHostToDevice, st));
+        RBF_CUDA(cudaStreamSynchronize(st));
+    }
 }
 
 void enqueue_ghost_fill(Problem &pb, void *U, cudaStream_t s) {
@@ -487,19 +546,17 @@ void enqueue_ghost_fill(Problem &pb, void *U, cudaStream_t s) {
                       (const int32_t *)gh.gidx.p, (const double *)gh.gw.p, (const int32_t *)gh.owner.p,
                       (const unsigned char *)gh.tb.p, (const int32_t *)gh.pos.p, (double *)gh.res.p,
                       pb.cp * pb.theta_bar * pb.theta_bar, pb.theta_bar, pb.g);
-        launch_kernel(ghost_apply<double>, g2, blk, s, pb.pdl, (double *)U, ng, rows,
-                      (const int32_t *)gh.comp_of.p, (const int64_t *)gh.comp_start.p, (const int64_t *)gh.inv_off.p,
-                      gh.n_comp, gh.n_class, (const double *)gh.inv.p, (const double *)gh.res.p,
-                      (const int64_t *)gh.grec.p, cf);
+        launch_kernel(ghost_apply_band<double>, g2, blk, s, pb.pdl, (double *)U, ng, rows, gh.n_class,
+                      (const int64_t *)gh.brow.p, (const int32_t *)gh.bcol.p, (const double *)gh.bval.p,
+                      (const double *)gh.res.p, (const int64_t *)gh.grec.p, cf);
     } else {
         launch_kernel(ghost_residual<float>, g1, blk, s, pb.pdl, (const float *)U, ng, rows, gh.npad,
                       (const int32_t *)gh.gidx.p, (const float *)gh.gw.p, (const int32_t *)gh.owner.p,
                       (const unsigned char *)gh.tb.p, (const int32_t *)gh.pos.p, (float *)gh.res.p,
                       (float)(pb.cp * pb.theta_bar * pb.theta_bar), (float)pb.theta_bar, (float)pb.g);
-        launch_kernel(ghost_apply<float>, g2, blk, s, pb.pdl, (float *)U, ng, rows,
-                      (const int32_t *)gh.comp_of.p, (const int64_t *)gh.comp_start.p, (const int64_t *)gh.inv_off.p,
-                      gh.n_comp, gh.n_class, (const float *)gh.inv.p, (const float *)gh.res.p,
-                      (const int64_t *)gh.grec.p, cf);
+        launch_kernel(ghost_apply_band<float>, g2, blk, s, pb.pdl, (float *)U, ng, rows, gh.n_class,
+                      (const int64_t *)gh.brow.p, (const int32_t *)gh.bcol.p, (const float *)gh.bval.p,
+                      (const float *)gh.res.p, (const int64_t *)gh.grec.p, cf);
     }
 }
 

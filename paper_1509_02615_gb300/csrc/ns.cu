@@ -40,6 +40,12 @@ struct NSArgs {
     const T *wx, *wz, *wd, *wh;
     const T *pibar;
     const unsigned char *flags;
+    // lattice storage (csrc/lattice.cu): class of each node (-1: per-node
+    // operators), and per class the relative index and the packed operators
+    // of every slot, [4][n_cls][SLQ][G][V] (null: per-node storage only)
+    const int32_t *lcls, *loff;
+    const T *lw;
+    int n_cls;
     int64_t n_prog, n_all;
     int SLQ;          // operand vectors per lane
     int stage;
@@ -57,6 +63,7 @@ struct Vec<float> {
     using I = int4;
     __device__ static float at(const float4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
     __device__ static int at(const int4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+    __device__ static int4 shift(const int4 &v, int d) { return make_int4(v.x + d, v.y + d, v.z + d, v.w + d); }
 };
 template <>
 struct Vec<double> {
@@ -65,6 +72,7 @@ struct Vec<double> {
     using I = int2;
     __device__ static double at(const double2 &v, int k) { return k == 0 ? v.x : v.y; }
     __device__ static int at(const int2 &v, int k) { return k == 0 ? v.x : v.y; }
+    __device__ static int2 shift(const int2 &v, int d) { return make_int2(v.x + d, v.y + d); }
 };
 
 constexpr int kPrefetchVec = 3;   // operand vectors per lane held in registers (prefetch variant)
@@ -74,7 +82,10 @@ constexpr int kPrefetchVec = 3;   // operand vectors per lane held in registers 
 // gathers one node record per neighbour.  PF > 0: the lane's operand vectors
 // (constant data) are loaded into registers before grid_dep_wait(), so they
 // stream in while the preceding ghost kernels finish; PF == 0 streams them.
-template <class T, int G, bool DIFF, int PF>
+// LAT: a node of a lattice class takes its operand vectors from the class
+// table (neighbour = node + offset); the lanes of a warp whose nodes share a
+// class read the same table entries, which stay in L1.
+template <class T, int G, bool DIFF, int PF, bool LAT>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && PF == 0) ? 4 : 1) ns_stage_kernel(NSArgs<T> a) {
     using VT = Vec<T>;
     using W = typename VT::W;
@@ -128,6 +139,16 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && PF == 0) ? 4 : 1) ns_s
 #pragma unroll
         for (int q = 0; q < R; ++q)
             if (q < a.SLQ) vec(jr[q], rx[q], rz[q], rd[q], rh[q]);
+    } else if (LAT && __ldg(a.lcls + i) >= 0) {
+        const int c = __ldg(a.lcls + i);
+        const I *lo = reinterpret_cast<const I *>(a.loff);
+        const W *lw = reinterpret_cast<const W *>(a.lw);
+        const int64_t ls = (int64_t)a.n_cls * a.SLQ * G;   // in vectors, between operators
+        int64_t off = (int64_t)c * a.SLQ * G + g;
+#pragma unroll 2
+        for (int q = 0; q < a.SLQ; ++q, off += G)
+            vec(VT::shift(__ldg(lo + off), (int)i), __ldg(lw + off), __ldg(lw + ls + off), __ldg(lw + 2 * ls + off),
+                __ldg(lw + 3 * ls + off));
     } else {
         int64_t off = off0;
 #pragma unroll 2
@@ -351,7 +372,12 @@ template <class T, int G, int PF>
 void launch_ns_g(const NSArgs<T> &a, cudaStream_t s, bool pdl) {
     constexpr bool kDiff = sizeof(T) == 4;   // FP32: difference form; FP64: plain sums
     const dim3 grid(div_up(a.n_prog * G, 256)), blk(256);
-    launch_kernel(ns_stage_kernel<T, G, kDiff, PF>, grid, blk, s, pdl, a);
+    if (a.lcls) {
+        if (PF == 0) launch_kernel(ns_stage_kernel<T, G, kDiff, 0, true>, grid, blk, s, pdl, a);
+        else RBF_FAIL(RBF_E_ARG, "the lattice storage has no prefetch variant");
+    } else {
+        launch_kernel(ns_stage_kernel<T, G, kDiff, PF, false>, grid, blk, s, pdl, a);
+    }
 }
 
 template <class T>
@@ -401,6 +427,12 @@ NSArgs<T> ns_args(Problem &pb) {
     a.wh = pw + 3 * total;
     a.pibar = (const T *)pb.pibar.p;
     a.flags = pb.flags.p;
+    if (pb.lat.enabled) {
+        a.lcls = pb.lat.cls.p;
+        a.loff = pb.lat.loff.p;
+        a.lw = (const T *)pb.lat.lw.p;
+        a.n_cls = pb.lat.n_cls;
+    }
     a.n_prog = pb.n_prog;
     a.n_all = pb.n_all;
     a.SLQ = pb.SLQ;
@@ -539,6 +571,7 @@ void pack_operators(Problem &pb) {
                                                                   dcomb.p, (float *)pb.pw.p, pb.pidx.p);
     RBF_CHECK_LAUNCH();
     RBF_CUDA(cudaStreamSynchronize(pb.st));
+    if (pb.lat.enabled) pack_lattice(pb, comb, nops);
 }
 
 void enqueue_rk4_step(Problem &pb, double t, double dt, void *U, cudaStream_t s, bool rec, int step) {
@@ -607,7 +640,7 @@ void autotune_threads_per_node(Problem &pb) {
         pb.G = G;
         pack_operators(pb);
         for (int pf : {0, kPrefetchVec}) {
-            if (pf > 0 && (pb.kind != kNS || pb.SLQ > kPrefetchVec)) continue;
+            if (pf > 0 && (pb.kind != kNS || pb.SLQ > kPrefetchVec || pb.lat.enabled)) continue;
             pb.pf = pf;
             float ms = 1e30f;
             for (int rep = 0; rep < 3; ++rep) {

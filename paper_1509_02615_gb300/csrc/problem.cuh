@@ -47,7 +47,16 @@ struct GhostPlan {
     DevBuf<int64_t> inv_off;     // [n_class][n_comp] offset of each inverse block
     DevBuf<unsigned char> inv;   // T [sum over class, comp of m^2]
     DevBuf<unsigned char> res;   // T [F][n_ghost] residual b - W_I u_I - W_B u_B
+    // banded inverse rows: row (class, position) keeps the entries of its
+    // W_G^{-1} row above 2^-8 eps of the row's largest (CSR)
+    DevBuf<int64_t> brow;        // [n_class * n_ghost + 1]
+    DevBuf<int32_t> bcol;        // position of each kept entry
+    DevBuf<unsigned char> bval;  // T value of each kept entry
+    int64_t band_nnz = 0;
 };
+
+// Builds gh.brow / bcol / bval from the dense inverse blocks.
+void build_ghost_bands(GhostPlan &gh, int precision, cudaStream_t st);
 
 // Persistent run mode: one cooperative launch runs all the steps of an
 // rbf_run (csrc/persistent.cu).  The nodes are split into compact blocks,
@@ -134,6 +143,22 @@ struct Problem {
     int run_mode = 1;             // RBF_RUN_GRAPH or RBF_RUN_PERSISTENT
     PersistPlan ps;
 
+    // Lattice operator storage (csrc/lattice.cu): one packed operator row per
+    // class of translated stencils, used by the stage kernels when enabled.
+    struct Lattice {
+        bool enabled = false, classified = false;
+        int min_members = 32;
+        int32_t n_cls = 0;
+        int64_t class_nodes = 0;      // nodes in classes (the rest keep per-node operators)
+        std::vector<int32_t> cls_host;
+        std::vector<int64_t> rep;     // first member of each class
+        std::vector<int32_t> rep_idx; // [n_cls][n] its stencil
+        std::vector<double> rep_w;    // [nops][n_cls][n] its FP64 weights
+        DevBuf<int32_t> cls;          // [n_prog] class of each node, -1: per-node operators
+        DevBuf<int32_t> loff;         // [n_cls][SLQ][G][V] relative index of each slot
+        DevBuf<unsigned char> lw;     // T [4][n_cls][SLQ][G][V] packed operators
+    } lat;
+
     float weight_build_ms = 0.f, ghost_setup_ms = 0.f;
     std::unique_ptr<EnsembleState> ens;
 
@@ -146,6 +171,9 @@ void enqueue_rk4_step(Problem &pb, double t, double dt, void *U, cudaStream_t s,
 void enqueue_rhs(Problem &pb, double t, void *U, void *dUdt, cudaStream_t s);
 void autotune_threads_per_node(Problem &pb);
 void pack_operators(Problem &pb);
+void pack_lattice(Problem &pb, const std::vector<double> &comb, int nops);
+int32_t lattice_classes(const int32_t *idx, const double *x, const double *z, int64_t n_prog, int n,
+                        double period_x, double h, int min_members, int32_t *cls);
 void build_ghost_plan(Problem &pb, const int32_t *kind_host, const int32_t *owner_host);
 void enqueue_ghost_fill(Problem &pb, void *U, cudaStream_t s);
 void minmax(Problem &pb, const void *U, double *out);

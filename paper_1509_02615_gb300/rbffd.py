@@ -99,6 +99,8 @@ SIGNATURES = [
     ("rbf_run_host", C.c_int, [_P, _D, _D, _I64, _P]),
     ("rbf_set_run_mode", C.c_int, [_P, _I32, _I32, _I32]),
     ("rbf_set_spin_limit", C.c_int, [_P, _I64]),
+    ("rbf_set_operator_storage", C.c_int, [_P, _I32, _I32, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
+    ("rbf_lattice_classes", C.c_int, [_P, _P, _P, _I64, _I64, _I32, _D, _D, _I32, _P, C.POINTER(C.c_int32)]),
     ("rbf_partition_blocks", C.c_int, [_P, _P, _I64, _I32, _P]),
     ("rbf_sync", C.c_int, [_P]),
     ("rbf_minmax", C.c_int, [_P, _P, _P]),
@@ -235,6 +237,14 @@ class Problem:
         """'graph', 'persistent' or 'auto' (see rbf_set_run_mode)."""
         _check(lib().rbf_set_run_mode(self._h, self.RUN_MODES[mode], int(lanes), int(ctas)))
 
+    def set_operator_storage(self, mode, threads_per_node=0):
+        """'per-node' (Sec. 3's rows) or 'lattice' (one row per class of
+        translated stencils); returns (nodes in classes, classes)."""
+        cn, nc = C.c_int64(0), C.c_int32(0)
+        code = {"per-node": 0, "lattice": 1}[mode]
+        _check(lib().rbf_set_operator_storage(self._h, code, threads_per_node, C.byref(cn), C.byref(nc)))
+        return cn.value, nc.value
+
     def set_spin_limit(self, polls):
         _check(lib().rbf_set_spin_limit(self._h, int(polls)))
 
@@ -283,6 +293,19 @@ def partition_blocks(x, z, parts):
     out = np.zeros(x.shape[0], np.int32)
     _check(lib().rbf_partition_blocks(_host_ptr(x), _host_ptr(z), x.shape[0], int(parts), _host_ptr(out)))
     return out
+
+
+def lattice_classes(idx, x, z, n_prog, period_x, h, min_members=32):
+    """Host-only lattice classes of given stencils (rbf_lattice_classes):
+    per node its class id (-1: irregular) and the class count."""
+    idx = np.ascontiguousarray(idx, np.int32)
+    x = np.ascontiguousarray(x, np.float64)
+    z = np.ascontiguousarray(z, np.float64)
+    cls = np.zeros(n_prog, np.int32)
+    nc = C.c_int32(0)
+    _check(lib().rbf_lattice_classes(_host_ptr(idx), _host_ptr(x), _host_ptr(z), n_prog, x.shape[0], idx.shape[1],
+                                     period_x, h, min_members, _host_ptr(cls), C.byref(nc)))
+    return cls, nc.value
 
 
 def hyperviscosity_gamma(c, h, k):
