@@ -118,6 +118,11 @@ int rbf_build_weights(const double *x, const double *z, int64_t n_all, const int
 typedef struct rbf_problem rbf_problem;
 
 /* Parameters of the Navier-Stokes problem (Sec. 6.2-6.3). */
+/* Operator storage of the stage kernels (rbf_ns_params.storage,
+ * rbf_set_operator_storage). */
+#define RBF_STORE_PER_NODE 0
+#define RBF_STORE_LATTICE 1
+
 typedef struct rbf_ns_params {
     int32_t n_sten;     /* stencil size n (37 in Sec. 6)                      */
     int32_t phs_p;      /* PHS exponent of d/dx, d/dz, Lap, BC operators (7)   */
@@ -128,7 +133,10 @@ typedef struct rbf_ns_params {
                            weights stored in FP32, FP32 RHS and RK4           */
     int32_t threads_per_node; /* 0 = autotuned (lanes per node and register
                                  prefetch); else 1, 2, 4 or 8 lanes        */
-    int32_t reserved;
+    int32_t storage;    /* RBF_STORE_PER_NODE (0, Sec. 3's rows) or
+                           RBF_STORE_LATTICE (1, one row per class of
+                           translated stencils; see rbf_set_operator_storage);
+                           the only way to choose it for an ensemble         */
     double period_x;    /* > 0: periodic in x with this period (m)            */
     double mu;          /* viscosity (m^2/s)                                  */
     double gamma;       /* hyperviscosity coefficient gamma >= 0              */
@@ -378,10 +386,6 @@ int rbf_set_run_mode(rbf_problem *pb, int32_t mode, int32_t lanes, int32_t ctas)
  */
 int rbf_partition_blocks(const double *x, const double *z, int64_t n, int32_t parts, int32_t *block_of);
 
-/* Operator storage of the stage kernels (rbf_set_operator_storage). */
-#define RBF_STORE_PER_NODE 0
-#define RBF_STORE_LATTICE 1
-
 /*
  * f4 (beyond the paper): how the graph-mode stage kernels store their
  * operators.  RBF_STORE_PER_NODE (the default) keeps one packed row of every
@@ -398,7 +402,8 @@ int rbf_partition_blocks(const double *x, const double *z, int64_t n, int32_t pa
  * receive the number of nodes in classes and of classes (0 for per-node
  * storage).  rbf_get_info's rhs_bytes_per_node follows the storage.  The
  * persistent run mode keeps its own operators and is not affected.
- * Synchronises the problem's stream.  RBF_E_ARG for an advection problem or
+ * Synchronises the problem's stream.  RBF_E_ARG for an advection problem, an
+ * ensemble (whose storage is chosen at creation, rbf_ns_params.storage) or
  * an unknown mode.
  */
 int rbf_set_operator_storage(rbf_problem *pb, int32_t mode, int32_t threads_per_node, int64_t *class_nodes,

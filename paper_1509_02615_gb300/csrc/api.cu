@@ -96,6 +96,26 @@ void choose_threads(Problem &pb, int requested) {
     }
 }
 
+}  // namespace
+
+// Algorithmic bytes of one Navier-Stokes node-RHS of the stage kernel.
+// Per-node storage: packed weights (4 operators) + index per slot, the
+// node's own values, U_n, the RK4 accumulator read+write, the stage output,
+// pibar and the flag byte.  Lattice storage: class nodes read a class id
+// instead of their operators, irregular nodes read both, and the class table
+// is read once per launch.
+double ns_rhs_bytes(const Problem &pb) {
+    const double ts = (double)pb.tsize(), slots = pb.n_slots;
+    const double rest = 4 * ts + 4 * ts + 8 * ts + 4 * ts + ts + 1;
+    const double ops = slots * (4 * ts + 4);
+    if (!pb.lat.enabled) return ops + rest;
+    const double cn = (double)pb.lat.class_nodes, N = (double)pb.n_prog;
+    const double table = (double)pb.lat.n_cls * pb.SLQ * pb.G * pb.V * (4 * ts + 4);
+    return 4 + rest + (N - cn) / N * ops + table / N;
+}
+
+namespace {
+
 void invalidate_graph(Problem &pb) {
     if (pb.graph) cudaGraphExecDestroy(pb.graph);
     pb.graph = nullptr;
@@ -269,6 +289,8 @@ void choose_run_mode(Problem &pb, int mode, int lanes, int ctas) {
 // step in their ensemble's buffers).
 void build_ns(Problem &pb, const rbf_ns_params &prm, const double *x, const double *z, int64_t n_prog,
           int64_t n_all, const int32_t *kind, const int32_t *ghost_owner, void *stream, bool with_scratch) {
+    RBF_REQUIRE(prm.storage == RBF_STORE_PER_NODE || prm.storage == RBF_STORE_LATTICE, "unknown storage mode %d",
+                prm.storage);
     RBF_REQUIRE(prm.precision == 64 || prm.precision == 32, "precision must be 64 or 32");
     RBF_REQUIRE(prm.n_sten >= 2, "stencil size must be >= 2");
     RBF_REQUIRE(prm.mu >= 0.0 && prm.gamma >= 0.0, "mu and gamma must be >= 0");
@@ -338,6 +360,7 @@ void build_ns(Problem &pb, const rbf_ns_params &prm, const double *x, const doub
 
     rbf::build_ghost_plan(pb, kind, ghost_owner);
     if (with_scratch) rbf::alloc_scratch(pb);
+    pb.lat.enabled = prm.storage == RBF_STORE_LATTICE;
     rbf::choose_threads(pb, prm.threads_per_node);
     if (with_scratch && prm.threads_per_node == 0) rbf::choose_run_mode(pb, RBF_RUN_AUTO, 0, 0);
     RBF_CUDA(cudaStreamSynchronize(pb.st));
@@ -521,7 +544,8 @@ int rbf_set_operator_storage(rbf_problem *h, int32_t mode, int32_t threads_per_n
     return rbf::guarded([&] {
         RBF_REQUIRE(h, "null problem");
         Problem &pb = h->impl;
-        RBF_REQUIRE(pb.kind == rbf::kNS, "operator storage applies to Navier-Stokes problems");
+        RBF_REQUIRE(pb.kind == rbf::kNS,
+                    "operator storage is switched on Navier-Stokes problems (an ensemble's is set at creation)");
         RBF_REQUIRE(mode == RBF_STORE_PER_NODE || mode == RBF_STORE_LATTICE, "unknown storage mode %d", mode);
         RBF_REQUIRE(threads_per_node == 0 || threads_per_node == 1 || threads_per_node == 2 ||
                         threads_per_node == 4 || threads_per_node == 8,
@@ -588,17 +612,12 @@ int rbf_get_info(const rbf_problem *h, rbf_info *out) {
             slots = s / (double)pb.n_prog;
         }
         if (pb.kind != rbf::kAdvection) {
-            // packed weights (4 operators) + index per slot, the node's own
-            // values, U_n, the RK4 accumulator read+write, the stage output,
-            // pibar and the flag byte
-            out->rhs_bytes_per_node = slots * (4 * ts + 4) + 4 * ts + 4 * ts + 8 * ts + 4 * ts + ts + 1;
-            if (pb.lat.enabled && pb.kind == rbf::kNS) {
-                // lattice storage: class nodes read a class id instead of their
-                // operators; irregular nodes read both; the class table once
-                const double cn = (double)pb.lat.class_nodes, N = (double)pb.n_prog;
-                const double table = (double)pb.lat.n_cls * pb.SLQ * pb.G * pb.V * (4 * ts + 4);
-                out->rhs_bytes_per_node = 4 + (4 * ts + 4 * ts + 8 * ts + 4 * ts + ts + 1) +
-                                          (N - cn) / N * slots * (4 * ts + 4) + table / N;
+            if (pb.kind == rbf::kEnsemble) {   // node-weighted mean over the members
+                double b = 0.0;
+                for (auto &m : pb.ens->members) b += rbf::ns_rhs_bytes(*m) * (double)m->n_prog;
+                out->rhs_bytes_per_node = b / (double)pb.n_prog;
+            } else {
+                out->rhs_bytes_per_node = rbf::ns_rhs_bytes(pb);
             }
             out->rhs_flops_per_node = slots * (12 * 2 + (pb.diff ? 4 : 0)) + 40 + 4 * 4;
         } else {

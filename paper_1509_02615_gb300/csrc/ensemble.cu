@@ -29,10 +29,13 @@ struct BlockDesc {
     const T *wx, *wz, *wd, *wh;
     const T *pibar;
     const unsigned char *flags;
+    const int32_t *lcls, *loff;   // member's lattice storage (null: per-node rows only)
+    const T *lw;
     int64_t n_prog;   // member's prognostic nodes (operand stride, node bound)
     int64_t rec0;     // member's first record in the concatenated state
     int32_t node0;    // first member node of this block
     int32_t SLQ;      // operand vectors per lane
+    int32_t n_cls;    // member's lattice classes
     double dt;
 };
 
@@ -54,6 +57,7 @@ struct VecE<float> {
     using I = int4;
     __device__ static float at(const float4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
     __device__ static int at(const int4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+    __device__ static int4 shift(const int4 &v, int d) { return make_int4(v.x + d, v.y + d, v.z + d, v.w + d); }
 };
 template <>
 struct VecE<double> {
@@ -62,12 +66,14 @@ struct VecE<double> {
     using I = int2;
     __device__ static double at(const double2 &v, int k) { return k == 0 ? v.x : v.y; }
     __device__ static int at(const int2 &v, int k) { return k == 0 ? v.x : v.y; }
+    __device__ static int2 shift(const int2 &v, int d) { return make_int2(v.x + d, v.y + d); }
 };
 
 // The stage kernel of Eqs. (uEq)-(piEq) with the RK4 update, for a block of
 // one ensemble member (same arithmetic and operand order as the single-problem
-// stage kernel with streamed operands).
-template <class T, int G, bool DIFF>
+// stage kernel with streamed operands).  LAT: members with lattice storage
+// take a class node's operands from the member's class table.
+template <class T, int G, bool DIFF, bool LAT>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) ens_stage_kernel(const BlockDesc<T> *__restrict__ descs, EnsArgs<T> a) {
     using VT = VecE<T>;
     using W = typename VT::W;
@@ -89,11 +95,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) ens_stage_kernel(
     Rec<T> fi = {0, 0, 0, 0};
     if (DIFF) fi = load_rec(U, i);
     T ux = 0, uz = 0, ud = 0, wx_ = 0, wz_ = 0, wd_ = 0, tx = 0, tz = 0, td = 0, px = 0, pz = 0, ph = 0;
-    int64_t off = off0;
-#pragma unroll 2
-    for (int q = 0; q < d.SLQ; ++q, off += stride) {
-        const I jv = __ldg(pidx + off);
-        const W cx = __ldg(wx + off), cz = __ldg(wz + off), cd = __ldg(wd + off), ch = __ldg(wh + off);
+    auto vec = [&](const I &jv, const W &cx, const W &cz, const W &cd, const W &ch) {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             Rec<T> r = load_rec(U, VT::at(jv, v));
@@ -104,6 +106,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) ens_stage_kernel(
             tx += x * r.t; tz += z * r.t; td += dd * r.t;
             px += x * r.p; pz += z * r.p; ph += h * r.p;
         }
+    };
+    const int cl = (LAT && d.lcls) ? __ldg(d.lcls + i) : -1;
+    if (LAT && cl >= 0) {
+        const I *lo = reinterpret_cast<const I *>(d.loff);
+        const W *lw = reinterpret_cast<const W *>(d.lw);
+        const int64_t ls = (int64_t)d.n_cls * d.SLQ * G;   // in vectors, between operators
+        int64_t off = (int64_t)cl * d.SLQ * G + g;
+#pragma unroll 2
+        for (int q = 0; q < d.SLQ; ++q, off += G)
+            vec(VT::shift(__ldg(lo + off), (int)i), __ldg(lw + off), __ldg(lw + ls + off), __ldg(lw + 2 * ls + off),
+                __ldg(lw + 3 * ls + off));
+    } else {
+        int64_t off = off0;
+#pragma unroll 2
+        for (int q = 0; q < d.SLQ; ++q, off += stride)
+            vec(__ldg(pidx + off), __ldg(wx + off), __ldg(wz + off), __ldg(wd + off), __ldg(wh + off));
     }
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) {
@@ -172,6 +190,12 @@ void fill_descs(Problem &pb) {
             d.wh = pw + 3 * total;
             d.pibar = (const T *)m.pibar.p;
             d.flags = m.flags.p;
+            if (m.lat.enabled) {
+                d.lcls = m.lat.cls.p;
+                d.loff = m.lat.loff.p;
+                d.lw = (const T *)m.lat.lw.p;
+                d.n_cls = m.lat.n_cls;
+            }
             d.n_prog = m.n_prog;
             d.rec0 = E.rec0[oi];
             d.node0 = (int32_t)n0;
@@ -189,8 +213,12 @@ void fill_descs(Problem &pb) {
 template <class T, int G>
 void launch_ens(Problem &pb, const EnsArgs<T> &a, int64_t nblocks, cudaStream_t s, bool pdl) {
     constexpr bool kDiff = sizeof(T) == 4;
-    launch_kernel(ens_stage_kernel<T, G, kDiff>, dim3((unsigned)nblocks), dim3(256), s, pdl,
-                  (const BlockDesc<T> *)pb.ens->descs.p, a);
+    if (pb.lat.enabled)
+        launch_kernel(ens_stage_kernel<T, G, kDiff, true>, dim3((unsigned)nblocks), dim3(256), s, pdl,
+                      (const BlockDesc<T> *)pb.ens->descs.p, a);
+    else
+        launch_kernel(ens_stage_kernel<T, G, kDiff, false>, dim3((unsigned)nblocks), dim3(256), s, pdl,
+                      (const BlockDesc<T> *)pb.ens->descs.p, a);
 }
 
 template <class T>
@@ -401,6 +429,9 @@ void build_ensemble(Problem &pb, const rbf_ns_params &common, int n, const rbf_e
     pb.cv = common.cv;
     pb.rd = common.rd;
     pb.diff = pb.precision == 32 ? 1 : 0;
+    RBF_REQUIRE(common.storage == RBF_STORE_PER_NODE || common.storage == RBF_STORE_LATTICE, "unknown storage mode %d",
+                common.storage);
+    pb.lat.enabled = common.storage == RBF_STORE_LATTICE;   // each member keeps its own class table
     pb.ens.reset(new EnsembleState());
     EnsembleState &E = *pb.ens;
     int64_t off_all = 0, off_prog = 0, off_ghost = 0;

@@ -31,7 +31,7 @@ class RBFError(RuntimeError):
 class NSParams(C.Structure):
     _fields_ = [("n_sten", C.c_int32), ("phs_p", C.c_int32), ("poly_l", C.c_int32), ("hv_k", C.c_int32),
                 ("hv_p", C.c_int32), ("precision", C.c_int32), ("threads_per_node", C.c_int32),
-                ("reserved", C.c_int32), ("period_x", C.c_double), ("mu", C.c_double), ("gamma", C.c_double),
+                ("storage", C.c_int32), ("period_x", C.c_double), ("mu", C.c_double), ("gamma", C.c_double),
                 ("theta_bar", C.c_double), ("g", C.c_double), ("cp", C.c_double), ("cv", C.c_double),
                 ("rd", C.c_double)]
 
@@ -241,7 +241,7 @@ class Problem:
         """'per-node' (Sec. 3's rows) or 'lattice' (one row per class of
         translated stencils); returns (nodes in classes, classes)."""
         cn, nc = C.c_int64(0), C.c_int32(0)
-        code = {"per-node": 0, "lattice": 1}[mode]
+        code = STORAGE[mode]
         _check(lib().rbf_set_operator_storage(self._h, code, threads_per_node, C.byref(cn), C.byref(nc)))
         return cn.value, nc.value
 
@@ -315,11 +315,14 @@ def hyperviscosity_gamma(c, h, k):
     return c * h ** (2 * k - 1)
 
 
+STORAGE = {"per-node": 0, "lattice": 1}
+
+
 def ns_problem(nodes: inp.NodeSet, precision=64, n=37, p=7, l=4, hv_k=3, hv_p=None, mu=75.0, gamma=None,
-               gamma_c=2.0 ** -6, threads_per_node=0, theta_bar=inp.THETA_BAR):
+               gamma_c=2.0 ** -6, threads_per_node=0, theta_bar=inp.THETA_BAR, storage="per-node"):
     """Navier-Stokes problem on a node set (Sec. 6.2-6.3 defaults)."""
     prm = NSParams(n_sten=n, phs_p=p, poly_l=l, hv_k=hv_k, hv_p=hv_p if hv_p else p, precision=precision,
-                   threads_per_node=threads_per_node, reserved=0, period_x=nodes.period_x, mu=mu,
+                   threads_per_node=threads_per_node, storage=STORAGE[storage], period_x=nodes.period_x, mu=mu,
                    gamma=hyperviscosity_gamma(gamma_c, nodes.h, hv_k) if gamma is None else gamma,
                    theta_bar=theta_bar, g=inp.G, cp=inp.CP, cv=inp.CV, rd=inp.RD)
     _torch()
@@ -417,11 +420,12 @@ class Ensemble(Problem):
         return v.value
 
 
-def ensemble_problem(members, precision=32, p=7, hv_k=3, mu=75.0, gamma_c=2.0 ** -6, theta_bar=inp.THETA_BAR):
+def ensemble_problem(members, precision=32, p=7, hv_k=3, mu=75.0, gamma_c=2.0 ** -6, theta_bar=inp.THETA_BAR,
+                     storage="per-node"):
     """Batched ensemble of density-current members (inputs.EnsembleMember)."""
     _torch()
     common = NSParams(n_sten=37, phs_p=p, poly_l=4, hv_k=hv_k, hv_p=p, precision=precision, threads_per_node=0,
-                      reserved=0, period_x=0.0, mu=mu, gamma=0.0, theta_bar=theta_bar, g=inp.G, cp=inp.CP,
+                      storage=STORAGE[storage], period_x=0.0, mu=mu, gamma=0.0, theta_bar=theta_bar, g=inp.G, cp=inp.CP,
                       cv=inp.CV, rd=inp.RD)
     arr = (EnsMember * len(members))()
     for r, m in enumerate(members):
