@@ -125,7 +125,7 @@ def kernel_source_hash(key=""):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(key, nodes=None):
+def profiled_traffic(key, nodes=None, algorithmic=None):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
@@ -139,6 +139,10 @@ def profiled_traffic(key, nodes=None):
         return None
     if nodes is not None and "dram_bytes_per_node" in e:
         return e["dram_bytes_per_node"] * nodes   # captured on a smaller launch of the same kernel
+    if algorithmic is not None and "dram_per_algorithmic_byte" in e:
+        # captured on another mix of the same kernel's units: scaled by its
+        # traffic per algorithmic byte
+        return e["dram_per_algorithmic_byte"] * algorithmic
     return e.get("dram_bytes_per_launch")
 
 
@@ -358,7 +362,7 @@ def ensemble_case(torch, args):
            "timed_global_steps": K, "ms": ms, "node_updates_to_900s": sum_over_ranks(ens.node_updates(-1), world),
            "threads_per_node": info["threads_per_node"],
            "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                        "frac": ach / pk["hbm_gbs"], "traffic": profiled_traffic("ens_stage_fp32", ens.n_prog),
+                        "frac": ach / pk["hbm_gbs"], "traffic": profiled_traffic("ens_stage_fp32", algorithmic=bpl),
                         "kernel": "ens_stage_kernel",
                         "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg,
                         "peak_source": f"{pk_kind} hbm_gbs"},
@@ -381,7 +385,8 @@ def ensemble_case(torch, args):
         "ms": lms, "avg_stage_kernel_ms": lavg, "speedup_vs_per_node": ms / lms,
         "rhs_bytes_per_node": li["rhs_bytes_per_node"], "threads_per_node": li["threads_per_node"],
         "roofline": {"bound": "hbm", "achieved": lbpl / (lavg / 1e3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": lbpl / (lavg / 1e3) / 1e9 / pk["hbm_gbs"], "traffic": None,
+                     "frac": lbpl / (lavg / 1e3) / 1e9 / pk["hbm_gbs"],
+                     "traffic": profiled_traffic("ens_stage_lattice_fp32", algorithmic=lbpl),
                      "algorithmic_bytes_per_launch": lbpl, "avg_launch_ms": lavg,
                      "peak_source": f"{pk_kind} hbm_gbs"},
         "rel_l2_vs_per_node_same_steps": diff, "finite": lfin, "build_s": build_s}
