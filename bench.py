@@ -371,6 +371,20 @@ def ensemble_case(torch, args):
     Ur = U.cpu()
     ens.close()
     del U
+    # the same members in FP64 (per-node storage): the plain-FP64 form the
+    # FP32 batched form is judged against, and the FP32 error after the same steps
+    e64 = rbffd.ensemble_problem(members, precision=64)
+    ms64, _, fin64, U64 = _time_ensemble(torch, e64, K)
+    upd64 = sum_over_ranks(e64.node_updates(K), world)
+    ms64 = max_over_ranks(ms64, world)
+    f32, f64 = Ur.double(), U64.cpu()
+    out["fp64"] = {"value": upd64 / (ms64 / 1e3), "unit": "node-updates/s", "ms": ms64, "finite": fin64,
+                   "fp32_speedup": (upd / (ms / 1e3)) / (upd64 / (ms64 / 1e3)),
+                   "fp32_rel_l2_vs_fp64_same_steps": [
+                       float(torch.linalg.vector_norm(f32[:, f] - f64[:, f]) / torch.linalg.vector_norm(f64[:, f]))
+                       for f in range(4)]}
+    e64.close()
+    del U64, f64
     t0 = time.perf_counter()
     lens = rbffd.ensemble_problem(members, precision=32, storage="lattice")
     build_s = time.perf_counter() - t0
@@ -408,7 +422,7 @@ def learned_case(torch, args):
     ds = learned.build_dataset(hc, ratio, seeds, 900.0)
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
-    mlp, loss = learned.train(ds, n_train, iters=3000, batch=4096, lr=2e-3)
+    mlp, loss = learned.train(ds, n_train, iters=30000, batch=4096, lr=2e-3)
     t_train = time.perf_counter() - t0
     alpha, scores = learned.select_alpha(ds, mlp, range(n_train, n_train + n_val))
     test = list(range(n_train + n_val, ns))
