@@ -13,6 +13,8 @@ the C ABI.
   the result is bit-identical.
 * On the 100 m hexagonal density current more than 95% of the nodes are in
   classes.
+* The switch rejects advection problems and leaves a persistent run (which
+  keeps its own operators) bit-identical.
 * A batched ensemble created with lattice storage matches the same ensemble
   with per-node storage member by member (FP64 < 1e-10, FP32 < 1e-5), and
   FP64 members match the oracle.
@@ -142,3 +144,25 @@ def test_ensemble_lattice_matches_per_node(prec, tol):
         if prec == 64 and r in (0, 1):
             ref = NSOracle(m.nodes, n=m.n, l=m.l).run(m.U0, 0.0, m.dt, m.n_steps)[:, :m.nodes.n_prog]
             assert max(rel(out["lattice"][r][f], ref[f]) for f in range(4)) < 1e-10
+
+
+def test_storage_switch_rules():
+    """The switch applies to Navier-Stokes problems only, and a persistent run
+    (which keeps its own operators) is unchanged by it, bit for bit."""
+    adv = rbffd.advection_problem(inp.unit_square_mirrored(16), precision=64)
+    with pytest.raises(rbffd.RBFError):
+        adv.set_operator_storage("lattice")
+    adv.close()
+    nodes = inp.density_current_nodes(800.0)
+    U0 = inp.density_current_state(nodes)
+    pb = rbffd.ns_problem(nodes, precision=32, threads_per_node=1)
+    pb.set_run_mode("persistent", lanes=1)
+    A = rbffd.state_tensor(U0, 32)
+    B = A.clone()
+    pb.run(0.0, 2.0, 10, A)
+    pb.set_operator_storage("lattice", threads_per_node=1)
+    pb.run(0.0, 2.0, 10, B)
+    pb.sync()
+    assert pb.info()["run_mode"] == 2
+    assert torch.equal(A, B)
+    pb.close()
