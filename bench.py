@@ -252,6 +252,44 @@ def fp64_peak_tflops(torch, n=4096, reps=5):
     return 2.0 * n ** 3 / (best / 1e3) / 1e12
 
 
+def weights_case(torch, h, peak_tflops):
+    """a2 alone: the FP64 weight build of the headline node set through the C
+    ABI (rbf_build_weights: d/dx, d/dz, Lap, d2/dx2, d2/dz2 and Delta^3, all
+    from r^7 with degree 4 and n = 37, so one augmented system per node with
+    K = 6 right-hand sides, as rbf_ns_create builds them), timed with CUDA
+    events after a warm-up build.  Algorithmic flops per node:
+    (2/3) S^3 + 2 K S^2 (LU of the S x S system and its K right-hand sides)."""
+    from paper_1509_02615_gb300 import inputs as inp
+    from paper_1509_02615_gb300 import rbffd
+    nodes = inp.density_current_nodes(h)
+    x = torch.as_tensor(nodes.x, device="cuda")
+    z = torch.as_tensor(nodes.z, device="cuda")
+    idx = rbffd.build_stencils(x, z, nodes.n_prog, 37, nodes.period_x)
+    ops = ("dx", "dz", "lap", "dxx", "dzz", "hv")
+    stream = torch.cuda.current_stream()
+
+    def build():
+        rbffd.build_weights(x, z, idx, 7, 4, ops, 3, nodes.period_x)
+
+    build()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    build()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    S = 37 + 15
+    flops = nodes.n_prog * ((2.0 / 3.0) * S ** 3 + 2.0 * len(ops) * S ** 2)
+    ach = flops / (ms / 1e3) / 1e12
+    return {"workload": f"FP64 weights of the {nodes.n_prog} prognostic nodes at {h:g} m (6 operators from r^7, "
+                        f"one augmented system of size S = {S} per node)",
+            "ms": ms, "nodes_per_s": nodes.n_prog / (ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": ach / peak_tflops, "algorithmic_flops": flops,
+                         "peak_source": "measured cuBLAS DGEMM 4096^3 in this run"}}
+
+
 def large_case(torch, args, flush):
     """The same density current at a finer spacing, whose FP32 working set is
     several times larger than L2: the stage kernel's HBM roofline."""
@@ -680,6 +718,7 @@ def main():
            "note": "rbf_run_host per RK4 step: pinned host state -> device, one RK4 step, device -> host"}
 
     fp64 = None
+    weights = None
     if not args.no_fp64 and args.precision == 32:
         n64, pb64, _ = make_problem(args.h, 64)
         U64 = rbffd.state_tensor(U0, 64)
@@ -695,6 +734,7 @@ def main():
             avg64 = float(np.mean(k64)) / 4.0
             flops = i64["rhs_flops_per_node"] * n64.n_prog
         p64 = fp64_peak_tflops(torch)
+        weights = weights_case(torch, args.h, p64)
         fp64 = {"value": 4.0 * n64.n_prog * len(s64) / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / len(s64),
                 "roofline": {"bound": "alu", "achieved": flops / (avg64 / 1e3) / 1e12, "peak": p64,
                              "unit": "TFLOP/s", "frac": flops / (avg64 / 1e3) / 1e12 / p64,
@@ -751,7 +791,8 @@ def main():
                 "gpu_launches": (1 if persistent else info["launches_per_step"]) * args.steps,
                 "setup": {"weight_build_ms": info["weight_build_ms"], "ghost_setup_ms": info["ghost_setup_ms"]},
                 "sustained_run": sustained,
-                "fp64": fp64, "roofline_large": large, "batched": batched, "learned": learned_form,
+                "fp64": fp64, "weights": weights, "roofline_large": large, "batched": batched,
+                "learned": learned_form,
                 "cpu_baseline": base,
                 "state_minmax": {"theta_min": mm[2, 0], "w_min": mm[1, 0], "w_max": mm[1, 1]}}
         print(json.dumps(line), flush=True)

@@ -330,12 +330,18 @@ void build_ns(Problem &pb, const rbf_ns_params &prm, const double *x, const doub
     const int nbase = (int)pb.ops.size();
     if (pb.hv_k > 0) pb.ops.push_back(RBF_OP_HV);
     pb.w64.alloc(pb.ops.size() * (size_t)n_prog * pb.n);
-    rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, pb.period_x, pb.p, pb.l, 0, pb.ops.data(),
-                       nbase, pb.w64.p, pb.st);
-    if (pb.hv_k > 0) {
-        int hv = RBF_OP_HV;
-        rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, pb.period_x, pb.hv_p, pb.l, pb.hv_k, &hv,
-                           1, pb.w64.p + (size_t)nbase * n_prog * pb.n, pb.st);
+    if (pb.hv_k > 0 && pb.hv_p == pb.p) {
+        // one augmented system serves every operator: one LU, six right-hand sides
+        rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, pb.period_x, pb.p, pb.l, pb.hv_k,
+                           pb.ops.data(), (int)pb.ops.size(), pb.w64.p, pb.st);
+    } else {
+        rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, pb.period_x, pb.p, pb.l, 0,
+                           pb.ops.data(), nbase, pb.w64.p, pb.st);
+        if (pb.hv_k > 0) {
+            int hv = RBF_OP_HV;
+            rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, pb.period_x, pb.hv_p, pb.l,
+                               pb.hv_k, &hv, 1, pb.w64.p + (size_t)nbase * n_prog * pb.n, pb.st);
+        }
     }
     RBF_CUDA(cudaEventRecord(e1, pb.st));
     RBF_CUDA(cudaEventSynchronize(e1));
@@ -453,12 +459,17 @@ int rbf_adv_create_flow(rbf_problem **out, const rbf_adv_params *prm, const doub
             pb.ops = {RBF_OP_DX, RBF_OP_DZ};
             if (pb.hv_k > 0) pb.ops.push_back(RBF_OP_HV);
             pb.w64.alloc(pb.ops.size() * (size_t)n_prog * pb.n);
-            rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, 0.0, pb.p, pb.l, 0, pb.ops.data(), 2, pb.w64.p,
-                               pb.st);
-            if (pb.hv_k > 0) {
-                int hv = RBF_OP_HV;
-                rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, 0.0, pb.hv_p, pb.l, pb.hv_k, &hv, 1,
-                                   pb.w64.p + 2 * (size_t)n_prog * pb.n, pb.st);
+            if (pb.hv_k > 0 && pb.hv_p == pb.p) {
+                rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, 0.0, pb.p, pb.l, pb.hv_k,
+                                   pb.ops.data(), (int)pb.ops.size(), pb.w64.p, pb.st);
+            } else {
+                rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, 0.0, pb.p, pb.l, 0, pb.ops.data(),
+                                   2, pb.w64.p, pb.st);
+                if (pb.hv_k > 0) {
+                    int hv = RBF_OP_HV;
+                    rbf::build_weights(pb.x.p, pb.z.p, pb.n_all, pb.idx.p, n_prog, pb.n, 0.0, pb.hv_p, pb.l, pb.hv_k,
+                                       &hv, 1, pb.w64.p + 2 * (size_t)n_prog * pb.n, pb.st);
+                }
             }
             RBF_CUDA(cudaEventRecord(e1, pb.st));
             RBF_CUDA(cudaEventSynchronize(e1));

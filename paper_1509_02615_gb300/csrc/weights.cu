@@ -19,6 +19,8 @@ namespace rbf {
 namespace {
 
 constexpr int kMaxOps = 6;
+constexpr int kMaxS = 160;                          // largest system size
+constexpr int kLaneCols = (kMaxS + kMaxOps + 31) / 32;   // columns a lane owns in the elimination
 
 struct WeightJob {
     int n, M, S, ld;       // stencil size, monomials, system size, leading dim
@@ -182,15 +184,50 @@ __global__ void weights_kernel(const double *__restrict__ x, const double *__res
                 A[bi * ld + j] = t;
             }
         __syncwarp();
+        // multipliers of the rows below the pivot, kept in the pivot column
         const double inv = 1.0 / A[kk * ld + kk];
-        // lanes own columns j > kk; rows below the pivot are updated in turn
-        for (int j0 = kk + 1; j0 < W; j0 += 32) {
-            int j = j0 + lane;
-            double prow = (j < W) ? A[kk * ld + j] : 0.0;
-            for (int i = kk + 1; i < S; ++i) {
-                double f = A[i * ld + kk] * inv;
-                if (j < W) A[i * ld + j] -= f * prow;
+        for (int i = kk + 1 + lane; i < S; i += 32) A[i * ld + kk] *= inv;
+        __syncwarp();
+        // lane owns columns lane + 32 c; the pivot row's entries stay in
+        // registers, and each pass updates four rows in every owned column
+        // (all loads of a pass before its stores, so they overlap)
+        double pr[kLaneCols];
+        bool own[kLaneCols];
+#pragma unroll
+        for (int c = 0; c < kLaneCols; ++c) {
+            const int j = lane + 32 * c;
+            own[c] = j > kk && j < W;
+            pr[c] = own[c] ? A[kk * ld + j] : 0.0;
+        }
+        int i = kk + 1;
+        for (; i + 3 < S; i += 4) {
+            const double m0 = A[i * ld + kk], m1 = A[(i + 1) * ld + kk];
+            const double m2 = A[(i + 2) * ld + kk], m3 = A[(i + 3) * ld + kk];
+            double v[kLaneCols][4];
+#pragma unroll
+            for (int c = 0; c < kLaneCols; ++c) {
+                if (!own[c]) continue;
+                const int j = lane + 32 * c;
+                v[c][0] = A[i * ld + j];
+                v[c][1] = A[(i + 1) * ld + j];
+                v[c][2] = A[(i + 2) * ld + j];
+                v[c][3] = A[(i + 3) * ld + j];
             }
+#pragma unroll
+            for (int c = 0; c < kLaneCols; ++c) {
+                if (!own[c]) continue;
+                const int j = lane + 32 * c;
+                A[i * ld + j] = v[c][0] - m0 * pr[c];
+                A[(i + 1) * ld + j] = v[c][1] - m1 * pr[c];
+                A[(i + 2) * ld + j] = v[c][2] - m2 * pr[c];
+                A[(i + 3) * ld + j] = v[c][3] - m3 * pr[c];
+            }
+        }
+        for (; i < S; ++i) {
+            const double m = A[i * ld + kk];
+#pragma unroll
+            for (int c = 0; c < kLaneCols; ++c)
+                if (own[c]) A[i * ld + lane + 32 * c] -= m * pr[c];
         }
         __syncwarp();
     }
@@ -238,7 +275,7 @@ void build_weights(const double *x, const double *z, int64_t n_all, const int32_
     job.n = n;
     job.M = (l + 1) * (l + 2) / 2;
     job.S = n + job.M;
-    RBF_REQUIRE(job.S <= 160, "system size n + (l+1)(l+2)/2 = %d exceeds 160", job.S);
+    RBF_REQUIRE(job.S <= kMaxS, "system size n + (l+1)(l+2)/2 = %d exceeds %d", job.S, kMaxS);
     RBF_REQUIRE(job.M <= n, "need at least (l+1)(l+2)/2 = %d stencil nodes, have %d", job.M, n);
     job.p = p;
     job.l = l;
