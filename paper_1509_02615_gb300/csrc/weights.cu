@@ -19,8 +19,7 @@ namespace rbf {
 namespace {
 
 constexpr int kMaxOps = 6;
-constexpr int kMaxS = 160;                          // largest system size
-constexpr int kLaneCols = (kMaxS + kMaxOps + 31) / 32;   // columns a lane owns in the elimination
+constexpr int kMaxS = 160;   // largest system size
 
 struct WeightJob {
     int n, M, S, ld;       // stencil size, monomials, system size, leading dim
@@ -127,12 +126,21 @@ __global__ void weights_kernel(const double *__restrict__ x, const double *__res
     for (int j = lane; j < n; j += 32) { xi[j] *= inv_s; eta[j] *= inv_s; }
     __syncwarp();
 
-    // assemble [A P | rhs; P^T 0 | rhs]
-    for (int e = lane; e < n * n; e += 32) {
-        int i = e / n, j = e - i * n;
-        double dx = xi[i] - xi[j], dz = eta[i] - eta[j];
-        double r2 = dx * dx + dz * dz;
-        A[i * ld + j] = (r2 == 0.0) ? 0.0 : rpow_odd(r2, sqrt(r2), job.p);
+    // assemble [A P | rhs; P^T 0 | rhs]; the PHS block is symmetric, so each
+    // pair (i <= j) is evaluated once (entries of the upper triangle walked
+    // row by row, 32 apart per lane)
+    {
+        int i = 0, j = lane;
+        while (i < n && j >= n) { j -= n - i - 1; ++i; }   // j - i counts from the diagonal
+        for (; i < n;) {
+            double dx = xi[i] - xi[j], dz = eta[i] - eta[j];
+            double r2 = dx * dx + dz * dz;
+            const double v = (r2 == 0.0) ? 0.0 : rpow_odd(r2, sqrt(r2), job.p);
+            A[i * ld + j] = v;
+            A[j * ld + i] = v;
+            j += 32;
+            while (i < n && j >= n) { j -= n - i - 1; ++i; }
+        }
     }
     for (int i = lane; i < n; i += 32) {
         int m = 0;
@@ -161,22 +169,28 @@ __global__ void weights_kernel(const double *__restrict__ x, const double *__res
     }
     __syncwarp();
 
-    // Gaussian elimination with partial pivoting on the S x (S + K) block
+    // Gaussian elimination with partial pivoting on the S x (S + K) block.
+    // The pivot search compares |a| through its bit pattern (for non-negative
+    // doubles the integer order is the numeric order), keeping the compares off
+    // the FP64 pipe; the rank-1 update of the trailing block spreads its entries
+    // over all 32 lanes.
     const int W = S + K;
     bool singular = false;
+    const long long kTiny = __double_as_longlong(1e-14);
+    const long long kInf = 0x7ff0000000000000LL;
     for (int kk = 0; kk < S; ++kk) {
-        double best = -1.0;
+        long long best = -1;
         int bi = kk;
         for (int i = kk + lane; i < S; i += 32) {
-            double v = fabs(A[i * ld + kk]);
+            const long long v = __double_as_longlong(A[i * ld + kk]) & 0x7fffffffffffffffLL;
             if (v > best) { best = v; bi = i; }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            double ob = __shfl_xor_sync(0xffffffffu, best, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
         }
-        if (!(best > 1e-14)) { singular = true; break; }
+        if (!(best > kTiny) || best >= kInf) { singular = true; break; }   // tiny, inf or NaN pivot
         if (bi != kk)
             for (int j = kk + lane; j < W; j += 32) {
                 double t = A[kk * ld + j];
@@ -188,46 +202,25 @@ __global__ void weights_kernel(const double *__restrict__ x, const double *__res
         const double inv = 1.0 / A[kk * ld + kk];
         for (int i = kk + 1 + lane; i < S; i += 32) A[i * ld + kk] *= inv;
         __syncwarp();
-        // lane owns columns lane + 32 c; the pivot row's entries stay in
-        // registers, and each pass updates four rows in every owned column
-        // (all loads of a pass before its stores, so they overlap)
-        double pr[kLaneCols];
-        bool own[kLaneCols];
-#pragma unroll
-        for (int c = 0; c < kLaneCols; ++c) {
-            const int j = lane + 32 * c;
-            own[c] = j > kk && j < W;
-            pr[c] = own[c] ? A[kk * ld + j] : 0.0;
-        }
-        int i = kk + 1;
-        for (; i + 3 < S; i += 4) {
-            const double m0 = A[i * ld + kk], m1 = A[(i + 1) * ld + kk];
-            const double m2 = A[(i + 2) * ld + kk], m3 = A[(i + 3) * ld + kk];
-            double v[kLaneCols][4];
-#pragma unroll
-            for (int c = 0; c < kLaneCols; ++c) {
-                if (!own[c]) continue;
-                const int j = lane + 32 * c;
-                v[c][0] = A[i * ld + j];
-                v[c][1] = A[(i + 1) * ld + j];
-                v[c][2] = A[(i + 2) * ld + j];
-                v[c][3] = A[(i + 3) * ld + j];
+        // A[i][j] -= m_i p_j over the (S-kk-1) x (W-kk-1) trailing block, its
+        // entries walked row by row, 32 apart per lane, two per pass
+        const int w = W - kk - 1;
+        if (w > 0) {
+            int i = kk + 1, j = kk + 1 + lane;
+            while (j >= W && i < S) { j -= w; ++i; }
+            while (i < S) {
+                int i2 = i, j2 = j + 32;
+                while (j2 >= W && i2 < S) { j2 -= w; ++i2; }
+                const double m0 = A[i * ld + kk], p0 = A[kk * ld + j], a0 = A[i * ld + j];
+                const bool two = i2 < S;
+                double m1 = 0.0, p1 = 0.0, a1 = 0.0;
+                if (two) { m1 = A[i2 * ld + kk]; p1 = A[kk * ld + j2]; a1 = A[i2 * ld + j2]; }
+                A[i * ld + j] = a0 - m0 * p0;
+                if (two) A[i2 * ld + j2] = a1 - m1 * p1;
+                i = i2;
+                j = j2 + 32;
+                while (j >= W && i < S) { j -= w; ++i; }
             }
-#pragma unroll
-            for (int c = 0; c < kLaneCols; ++c) {
-                if (!own[c]) continue;
-                const int j = lane + 32 * c;
-                A[i * ld + j] = v[c][0] - m0 * pr[c];
-                A[(i + 1) * ld + j] = v[c][1] - m1 * pr[c];
-                A[(i + 2) * ld + j] = v[c][2] - m2 * pr[c];
-                A[(i + 3) * ld + j] = v[c][3] - m3 * pr[c];
-            }
-        }
-        for (; i < S; ++i) {
-            const double m = A[i * ld + kk];
-#pragma unroll
-            for (int c = 0; c < kLaneCols; ++c)
-                if (own[c]) A[i * ld + lane + 32 * c] -= m * pr[c];
         }
         __syncwarp();
     }
