@@ -410,7 +410,7 @@ def ensemble_case(torch, args):
     ens.close()
     del U
     # the same members in FP64 (per-node storage): the plain-FP64 form the
-    # FP32 batched form is judged against, and the FP32 error after the same steps
+    # FP32 batched form is compared with, and the FP32 error after the same steps
     e64 = rbffd.ensemble_problem(members, precision=64)
     ms64, _, fin64, U64 = _time_ensemble(torch, e64, K)
     upd64 = sum_over_ranks(e64.node_updates(K), world)

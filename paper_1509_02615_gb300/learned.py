@@ -135,6 +135,6 @@ def run_errors(ds: Dataset, mlp, runs, alpha):
 
 def select_alpha(ds: Dataset, mlp, val_runs, candidates=ALPHA_CANDIDATES):
     """Strength with the smallest mean validation error (the uncorrected
-    solver judges the correction: it is one of the candidates)."""
+    solver is the reference for the correction: it is one of the candidates)."""
     scores = [(float(np.mean(run_errors(ds, mlp, val_runs, a))), a) for a in candidates]
     return min(scores)[1], scores

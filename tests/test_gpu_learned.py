@@ -121,7 +121,7 @@ def test_correction_on_held_out_seeds():
     """800 m coarse runs corrected by an MLP trained on 200 m FP64 runs
     restricted to the coarse nodes (10 training seeds); the per-field strength
     is chosen on 3 validation seeds, with the uncorrected solver as a
-    candidate; 3 held-out seeds are judged at 900 s against the restricted
+    candidate; 3 held-out seeds are scored at 900 s against the restricted
     200 m reference.  The corrected error must not exceed the uncorrected one
     (2% slack for the validation-to-test spread)."""
     seeds = inp.learned_correction_seeds(16, seed=1)
