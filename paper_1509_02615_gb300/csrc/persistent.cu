@@ -869,14 +869,19 @@ bool persistent_plan(Problem &pb, int G, int ctas) {
     if (threads > 1024) return false;
     RBF_CUDA(cudaStreamSynchronize(pb.st));
 
-    // operators packed for G lanes (beside the launch-per-stage packing)
+    // operators packed for G lanes (beside the launch-per-stage packing); the
+    // lattice tables of the stage kernels are not repacked (this kernel keeps
+    // per-node operators), so they stay valid for the launch-per-stage lanes
     const int G0 = pb.G, pf0 = pb.pf, SLQ0 = pb.SLQ, SL0 = pb.SL, V0 = pb.V;
+    const bool lat0 = pb.lat.enabled;
     DevBuf<int32_t> pidx0 = std::move(pb.pidx);
     DevBuf<unsigned char> pw0 = std::move(pb.pw);
+    pb.lat.enabled = false;
     auto restore = [&] {
         pb.pidx = std::move(pidx0);
         pb.pw = std::move(pw0);
         pb.G = G0; pb.pf = pf0; pb.SLQ = SLQ0; pb.SL = SL0; pb.V = V0;
+        pb.lat.enabled = lat0;
     };
     std::vector<int32_t> hp;
     std::vector<unsigned char> hw;

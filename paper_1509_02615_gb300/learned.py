@@ -113,8 +113,9 @@ def rel_l2(a, b):
 
 # per-field correction strengths tried on the validation runs; all-zero is the
 # uncorrected solver, the fallback when no strength helps
-ALPHA_CANDIDATES = ((0.0, 0.0, 0.0, 0.0), (0.0, 0.0, 0.25, 0.0), (0.0, 0.0, 0.5, 0.0), (0.0, 0.0, 1.0, 0.0),
-                    (0.25, 0.25, 0.25, 0.0), (0.5, 0.5, 0.5, 0.0))
+ALPHA_CANDIDATES = ((0.0, 0.0, 0.0, 0.0), (0.0, 0.0, 0.125, 0.0), (0.0, 0.0, 0.25, 0.0), (0.0, 0.0, 0.375, 0.0),
+                    (0.0, 0.0, 0.5, 0.0), (0.0, 0.0, 0.75, 0.0), (0.0, 0.0, 1.0, 0.0), (0.25, 0.25, 0.25, 0.0),
+                    (0.5, 0.5, 0.5, 0.0))
 
 
 def run_errors(ds: Dataset, mlp, runs, alpha):

@@ -166,3 +166,23 @@ def test_storage_switch_rules():
     assert pb.info()["run_mode"] == 2
     assert torch.equal(A, B)
     pb.close()
+
+
+def test_lattice_tables_survive_run_mode_autotuning():
+    """A lattice problem with autotuned lanes and run mode (the persistent
+    plans tried at creation pack operators for their own lane counts) keeps
+    graph-mode tables that match its lanes: its graph-mode right-hand side
+    equals the per-node problem's to FP32 rounding."""
+    nodes = inp.density_current_nodes(400.0)
+    U0 = inp.density_current_state(nodes)
+    out = {}
+    for storage in ("per-node", "lattice"):
+        pb = rbffd.ns_problem(nodes, precision=32, storage=storage)
+        pb.set_run_mode("persistent", lanes=2)    # plans for another lane count, then back
+        pb.set_run_mode("graph")
+        U = rbffd.state_tensor(U0, 32)
+        out[storage] = rbffd.fields(pb.rhs(0.0, U))
+        pb.close()
+    errs = [rel(out["lattice"][f], out["per-node"][f]) for f in range(4)]
+    print("lattice after run-mode planning vs per-node RHS", ["%.1e" % e for e in errs])
+    assert max(errs) < 1e-5
