@@ -14,7 +14,8 @@ timed steps; each step is timed alone with CUDA events on the problem's
 stream.  The FP64 form of the same workload is reported under "fp64".
 
 --impl reference times the FP64 CPU oracle (the only other implementation of
-the method here) on a bounded sample of the same workload.
+the method here) on a bounded sample of the same workload: one 1/8-width strip
+per host core.
 """
 import argparse
 import hashlib
@@ -588,36 +589,57 @@ def cpu_baseline(h, budget_s=12.0):
             "oracle_setup_s": setup_s}
 
 
+def _oracle_rk4_steps(args):
+    """W untimed and K timed oracle RK4 steps on one strip: (nodes, seconds).
+    Runs in a spawned worker process."""
+    h, warmup, steps = args
+    nodes, o, U, _ = _oracle_strip(h)
+    dt = h / 400.0
+    for s in range(warmup):
+        U = o.rk4_step((1 + s) * dt, dt, U)
+    t0 = time.perf_counter()
+    for s in range(steps):
+        U = o.rk4_step((1 + warmup + s) * dt, dt, U)
+    return nodes.n_prog, time.perf_counter() - t0
+
+
 def run_reference(args, rank, world):
-    """The oracle arm: W untimed and K timed RK4 steps of the FP64 oracle on the
-    1/8-width strip of the workload (same spacing, stencils, walls), single
-    core; one step is four right-hand sides with their ghost solves."""
+    """The oracle arm: W untimed and K timed RK4 steps of the FP64 oracle on
+    1/8-width strips of the workload (same spacing, stencils, walls), one
+    strip per host core in spawned single-threaded processes; one step is four
+    right-hand sides with their ghost solves.  The rate sums the strips'
+    node-RHS/s."""
     if rank != 0:
         return
-    from oracle.ns import NSOracle
-    from paper_1509_02615_gb300 import inputs as inp
+    import multiprocessing as mp
     t_start = time.perf_counter()
-    width = 25600.0 / 8.0
-    nodes = inp.lattice_nodes("hex", -width, width, 0.0, 6400.0, args.h, True)
-    o = NSOracle(nodes)
-    dt = args.h / 400.0
-    U = inp.density_current_state(nodes)
-    for s in range(args.warmup):
-        U = o.rk4_step(s * dt, dt, U)
-    t0 = time.perf_counter()
-    for s in range(args.steps):
-        U = o.rk4_step((args.warmup + s) * dt, dt, U)
-    el = time.perf_counter() - t0
-    value = 4.0 * nodes.n_prog * args.steps / el
-    sample = (f"FP64 oracle RK4 steps (ghost solves + sparse DM products) on a periodic strip of the workload, 1/8 of "
-              f"its width ({nodes.n_prog} of 38400 nodes, same h, stencils and walls): {args.warmup} untimed + "
-              f"{args.steps} timed steps in {el:.2f} s, single-threaded scipy.sparse")
+    cores = os.cpu_count() or 1
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    for k in keys:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_rk4_steps, [(args.h, args.warmup, args.steps)] * cores)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    value = sum(4.0 * n * args.steps / el for n, el in res)
+    ms_step = 1e3 * float(np.mean([el for _, el in res])) / max(args.steps, 1)
+    n_strip = res[0][0]
+    sample = (f"FP64 oracle RK4 steps (ghost solves + sparse DM products) on periodic strips of the workload, 1/8 of "
+              f"its width ({n_strip} of 38400 nodes, same h, stencils and walls), one strip per core in {cores} "
+              f"spawned single-threaded processes: {args.warmup} untimed + {args.steps} timed steps each, "
+              f"{ms_step:.1f} ms per step per strip")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(args.steps, 1),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": "fp64 oracle", "l2": "n/a (CPU)",
-                       "sample_nodes": nodes.n_prog},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                       "sample_nodes": n_strip * cores},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t_start}
     print(json.dumps(line), flush=True)
