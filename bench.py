@@ -764,7 +764,8 @@ def main():
                              "frac_of_nominal": flops / (avg64 / 1e3) / 1e12 / 1.25, "avg_launch_ms": avg64,
                              "hbm_GBps": i64["rhs_bytes_per_node"] * n64.n_prog / (avg64 / 1e3) / 1e9},
                 "threads_per_node": i64["threads_per_node"],
-                "run_mode": "persistent" if i64["run_mode"] == 2 else "graph"}
+                "run_mode": "persistent" if i64["run_mode"] == 2 else "graph",
+                "persistent_lanes": i64["persist_lanes"], "persistent_ctas": i64["persist_ctas"]}
         # accuracy of the FP32 form: the whole run to 900 s in both precisions
         # (the FP64 path matches the FP64 oracle to ~1e-12), per-field
         # relative l2 of FP32 against FP64 at t_final
