@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--persistent-ctas", type=int, default=0, help="CTAs with --run-mode persistent (0: one per SM)")
     ap.add_argument("--ens-runs", type=int, default=256, help="ensemble members (0 = skip the batched case)")
     ap.add_argument("--ens-steps", type=int, default=40, help="timed global RK4 steps of the ensemble")
+    ap.add_argument("--ens-threads", type=int, default=0, choices=(0, 1, 2, 4),
+                    help="lanes per node of the batched ensembles (0 = autotuned)")
     ap.add_argument("--learned", type=int, default=1, help="1 = measure the learned coarse-grid correction")
     ap.add_argument("--learned-coarse", type=float, default=400.0)
     ap.add_argument("--learned-ratio", type=int, default=4)
@@ -126,9 +128,10 @@ def kernel_source_hash(key=""):
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(key, nodes=None, algorithmic=None):
+def profiled_traffic(key, nodes=None, algorithmic=None, **launch):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+    the current kernel source and the same launch shape (the ``launch``
+    keywords, e.g. threads_per_node, that the summary records); else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -137,6 +140,8 @@ def profiled_traffic(key, nodes=None, algorithmic=None):
         return None
     e = d.get(key)
     if not e or e.get("source_hash") != kernel_source_hash(key):
+        return None
+    if any(k in e and e[k] != v for k, v in launch.items()):
         return None
     if nodes is not None and "dram_bytes_per_node" in e:
         return e["dram_bytes_per_node"] * nodes   # captured on a smaller launch of the same kernel
@@ -310,7 +315,8 @@ def large_case(torch, args, flush):
            "node_rhs_per_s": 4.0 * nodes.n_prog * steps / (float(sum(step_ms)) / 1e3),
            "ms_per_step": float(sum(step_ms)) / steps,
            "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                        "frac": ach / pk["hbm_gbs"], "traffic": profiled_traffic(f"ns_stage_fp32_hex{int(args.large_h)}"),
+                        "frac": ach / pk["hbm_gbs"], "traffic": profiled_traffic(f"ns_stage_fp32_hex{int(args.large_h)}",
+                                                                   threads_per_node=info["threads_per_node"]),
                         "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg,
                         "peak_source": f"{pk_kind} hbm_gbs"},
            "threads_per_node": info["threads_per_node"], "prefetch": info["prefetch"],
@@ -337,7 +343,8 @@ def large_case(torch, args, flush):
         "classes": nc, "class_nodes": cn, "class_fraction": cn / nodes.n_prog,
         "rhs_bytes_per_node": li["rhs_bytes_per_node"], "threads_per_node": li["threads_per_node"],
         "roofline": {"bound": "hbm", "achieved": lach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                     "frac": lach / pk["hbm_gbs"], "traffic": profiled_traffic(f"ns_stage_lattice_fp32_hex{int(args.large_h)}"),
+                     "frac": lach / pk["hbm_gbs"], "traffic": profiled_traffic(f"ns_stage_lattice_fp32_hex{int(args.large_h)}",
+                                                                threads_per_node=li["threads_per_node"]),
                      "algorithmic_bytes_per_launch": lbpl, "avg_launch_ms": lavg,
                      "peak_source": f"{pk_kind} hbm_gbs",
                      "note": "algorithmic bytes of the lattice storage: class id + records, no per-node operators"},
@@ -386,7 +393,7 @@ def ensemble_case(torch, args):
     every = inp.ensemble_members(args.ens_runs, seed=0)
     members = shard_members(every, rank, world)
     t_gen = time.perf_counter() - t0
-    ens = rbffd.ensemble_problem(members, precision=32)
+    ens = rbffd.ensemble_problem(members, precision=32, threads_per_node=args.ens_threads)
     info = ens.info()
     K = args.ens_steps
     ms, avg, finite, U = _time_ensemble(torch, ens, K)
@@ -401,7 +408,8 @@ def ensemble_case(torch, args):
            "timed_global_steps": K, "ms": ms, "node_updates_to_900s": sum_over_ranks(ens.node_updates(-1), world),
            "threads_per_node": info["threads_per_node"],
            "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                        "frac": ach / pk["hbm_gbs"], "traffic": profiled_traffic("ens_stage_fp32", algorithmic=bpl),
+                        "frac": ach / pk["hbm_gbs"], "traffic": profiled_traffic("ens_stage_fp32", algorithmic=bpl,
+                                                                   threads_per_node=info["threads_per_node"]),
                         "kernel": "ens_stage_kernel",
                         "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg,
                         "peak_source": f"{pk_kind} hbm_gbs"},
@@ -412,7 +420,7 @@ def ensemble_case(torch, args):
     del U
     # the same members in FP64 (per-node storage): the plain-FP64 form the
     # FP32 batched form is compared with, and the FP32 error after the same steps
-    e64 = rbffd.ensemble_problem(members, precision=64)
+    e64 = rbffd.ensemble_problem(members, precision=64, threads_per_node=args.ens_threads)
     ms64, _, fin64, U64 = _time_ensemble(torch, e64, K)
     upd64 = sum_over_ranks(e64.node_updates(K), world)
     ms64 = max_over_ranks(ms64, world)
@@ -425,7 +433,7 @@ def ensemble_case(torch, args):
     e64.close()
     del U64, f64
     t0 = time.perf_counter()
-    lens = rbffd.ensemble_problem(members, precision=32, storage="lattice")
+    lens = rbffd.ensemble_problem(members, precision=32, storage="lattice", threads_per_node=args.ens_threads)
     build_s = time.perf_counter() - t0
     li = lens.info()
     lms, lavg, lfin, LU = _time_ensemble(torch, lens, K)
@@ -439,7 +447,8 @@ def ensemble_case(torch, args):
         "rhs_bytes_per_node": li["rhs_bytes_per_node"], "threads_per_node": li["threads_per_node"],
         "roofline": {"bound": "hbm", "achieved": lbpl / (lavg / 1e3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": lbpl / (lavg / 1e3) / 1e9 / pk["hbm_gbs"],
-                     "traffic": profiled_traffic("ens_stage_lattice_fp32", algorithmic=lbpl),
+                     "traffic": profiled_traffic("ens_stage_lattice_fp32", algorithmic=lbpl,
+                                                 threads_per_node=li["threads_per_node"]),
                      "algorithmic_bytes_per_launch": lbpl, "avg_launch_ms": lavg,
                      "peak_source": f"{pk_kind} hbm_gbs"},
         "rel_l2_vs_per_node_same_steps": diff, "finite": lfin, "build_s": build_s}
@@ -706,7 +715,10 @@ def main():
     achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
     key = f"{'persistent' if persistent else 'ns_stage'}_fp{args.precision}_hex{int(args.h)}"
     roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": profiled_traffic(key), "kernel": kernel,
+            "frac": achieved / pk["hbm_gbs"], "traffic": profiled_traffic(key, **({"persistent_lanes": info["persist_lanes"],
+                                                  "persistent_ctas": info["persist_ctas"]} if persistent else
+                                                 {"threads_per_node": info["threads_per_node"]})),
+            "kernel": kernel,
             "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
             "kernel_share_of_step": share, "peak_source": f"{pk_kind} hbm_gbs"}
 

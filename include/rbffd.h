@@ -235,7 +235,8 @@ typedef struct rbf_ens_member {
  * kind concatenates the members' prognostic kinds and ghost_owner their ghost
  * owners (member-local indices), as for rbf_ns_create.  The state is the
  * members' node-major records concatenated in the same order
- * ([sum n_all][4]).  Threads per node are autotuned for the whole ensemble.
+ * ([sum n_all][4]).  common.threads_per_node = 0 autotunes the lanes per node
+ * for the whole ensemble; 1, 2 or 4 fixes them (RBF_E_ARG otherwise).
  */
 int rbf_ens_create(rbf_problem **out, const rbf_ns_params *common, int32_t n_members,
                    const rbf_ens_member *members, const double *x, const double *z, const int32_t *kind,

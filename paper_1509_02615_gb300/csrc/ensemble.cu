@@ -417,6 +417,9 @@ void build_ensemble(Problem &pb, const rbf_ns_params &common, int n, const rbf_e
     RBF_REQUIRE(n >= 1, "an ensemble needs at least one member");
     RBF_REQUIRE(common.precision == 32 || common.precision == 64, "precision must be 64 or 32");
     RBF_REQUIRE(x && z && kind && owner && mem, "null argument");
+    RBF_REQUIRE(common.threads_per_node == 0 || common.threads_per_node == 1 || common.threads_per_node == 2 ||
+                    common.threads_per_node == 4,
+                "ensemble threads per node must be 0 (autotune), 1, 2 or 4");
     pb.kind = kEnsemble;
     pb.F = 4;
     pb.precision = common.precision;
@@ -483,7 +486,8 @@ void build_ensemble(Problem &pb, const rbf_ns_params &common, int n, const rbf_e
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     for (auto &m : E.members) pb.ghost_setup_ms += m->ghost_setup_ms;
-    autotune_ensemble(pb);
+    if (common.threads_per_node == 0) autotune_ensemble(pb);
+    else set_ens_threads(pb, common.threads_per_node);
     // FP64 weights and raw stencils were only needed to build and repack
     for (auto &m : E.members) {
         m->w64.release();

@@ -192,7 +192,10 @@ __global__ void __launch_bounds__(256) ghost_residual(const T *__restrict__ U, i
 // computing every field of that boundary-operator class.  The kept entries
 // of row (class, q) are bval[brow[r] .. brow[r+1]) at positions bcol
 // (absolute, within the component), r = class * ng + q; the first
-// kBandPf * 32 entries of a row are loaded before the wait.
+// kBandPf * 32 entries of a row are loaded before the wait.  Lanes past the
+// row's end skip the product instead of multiplying a zero by some other
+// component's residual: a non-finite residual (a member that has blown up
+// in a batched ensemble) then stays within its own component.
 constexpr int kBandPf = 4;
 
 template <class T>
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(256) ghost_apply_band(T *__restrict__ U, int64
         const int64_t e = b0 + lane + 32 * t;
         const bool in = e < b1;
         a[t] = in ? __ldg(bval + e) : (T)0;
-        col[t] = in ? __ldg(bcol + e) : 0;
+        col[t] = in ? __ldg(bcol + e) : -1;
     }
     const int fm = cls == 0 ? cls_fields.x : cls == 1 ? cls_fields.y : cls == 2 ? cls_fields.z : cls_fields.w;
     grid_dep_wait();
@@ -228,7 +231,8 @@ __global__ void __launch_bounds__(256) ghost_apply_band(T *__restrict__ U, int64
         const T *rr = res + f * ng;
         T s = 0;
 #pragma unroll
-        for (int t = 0; t < kBandPf; ++t) s += a[t] * rr[col[t]];
+        for (int t = 0; t < kBandPf; ++t)
+            if (col[t] >= 0) s += a[t] * rr[col[t]];
         for (int64_t e = b0 + lane + 32 * kBandPf; e < b1; e += 32) s += __ldg(bval + e) * rr[__ldg(bcol + e)];
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0) U[grec[q] * 4 + f] = s;

@@ -504,10 +504,17 @@ def perturbed_density_current(nodes: NodeSet, seed: int) -> np.ndarray:
 # Batched ensembles of density-current runs of uneven size
 # ----------------------------------------------------------------------------
 
-# (stencil size, polynomial degree) choices of ensemble members; every pair is
-# linearly stable at dt = h/400 with the hyperviscosity of Sec. 5.3 (n = 21
-# is not: the RK4 amplification of its worst mode exceeds 1.09)
+# (stencil size, polynomial degree) choices of ensemble members, with the
+# hyperviscosity of Sec. 5.3 and dt = h/400 (n = 21 is left out: the RK4
+# amplification of its worst linear mode exceeds 1.09 at 800 m)
 ENSEMBLE_STENCILS = ((31, 3), (37, 4), (45, 4), (56, 5), (75, 5))
+
+# (layout, n, l) pairs the draw skips because those runs blow up before 900 s:
+# on the Cartesian lattice n = 75 with l = 5 has a real growing mode of the
+# operator linearised about rest at 400 m (RK4 amplification 1.17 per step)
+# and goes non-finite at every spacing from 50 to 400 m, and n = 31 with
+# l = 3 goes non-finite after about 4,800 steps at 50 m.
+ENSEMBLE_UNSTABLE = (("cart", 75, 5), ("cart", 31, 3))
 
 
 @dataclasses.dataclass
@@ -537,13 +544,15 @@ def density_current_member(h, layout, n, l, seed, t_end=900.0):
 def ensemble_members(n_runs=256, seed=0, spacings=(50.0, 100.0, 200.0, 400.0),
                      layouts=("cart", "hex", "scattered"), stencils=ENSEMBLE_STENCILS, t_end=900.0):
     """Seeded draw of ensemble members: spacing, layout, stencil size and
-    perturbation of each run."""
+    perturbation of each run.  The stencil is drawn among the choices that
+    are stable on the drawn layout (ENSEMBLE_UNSTABLE)."""
     rng = np.random.default_rng(seed)
     out = []
     for r in range(n_runs):
         h = float(spacings[rng.integers(len(spacings))])
         layout = str(layouts[rng.integers(len(layouts))])
-        n, l = stencils[rng.integers(len(stencils))]
+        ok = [s for s in stencils if (layout,) + tuple(s) not in ENSEMBLE_UNSTABLE]
+        n, l = ok[rng.integers(len(ok))]
         out.append(density_current_member(h, layout, n, l, seed=seed * 100003 + r, t_end=t_end))
     return out
 

@@ -421,10 +421,12 @@ class Ensemble(Problem):
 
 
 def ensemble_problem(members, precision=32, p=7, hv_k=3, mu=75.0, gamma_c=2.0 ** -6, theta_bar=inp.THETA_BAR,
-                     storage="per-node"):
-    """Batched ensemble of density-current members (inputs.EnsembleMember)."""
+                     storage="per-node", threads_per_node=0):
+    """Batched ensemble of density-current members (inputs.EnsembleMember);
+    threads_per_node 0 autotunes the lanes per node."""
     _torch()
-    common = NSParams(n_sten=37, phs_p=p, poly_l=4, hv_k=hv_k, hv_p=p, precision=precision, threads_per_node=0,
+    common = NSParams(n_sten=37, phs_p=p, poly_l=4, hv_k=hv_k, hv_p=p, precision=precision,
+                      threads_per_node=threads_per_node,
                       storage=STORAGE[storage], period_x=0.0, mu=mu, gamma=0.0, theta_bar=theta_bar, g=inp.G, cp=inp.CP,
                       cv=inp.CV, rd=inp.RD)
     arr = (EnsMember * len(members))()

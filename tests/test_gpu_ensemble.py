@@ -79,3 +79,37 @@ def test_ensemble_partial_run_counts():
     ens.run(3, U)
     mm = ens.minmax(U)
     assert np.all(np.isfinite(mm))
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_blown_up_member_leaves_the_others_untouched(precision):
+    """A non-finite value on a wall node of the first member in run order
+    (the owner of ghost position 0 in the merged ghost systems) must not reach
+    any other member: the others end bitwise equal to the same ensemble run
+    without it."""
+    mem = [inp.density_current_member(800.0, lay, n, l, seed=5 + i, t_end=8.0)
+           for i, (lay, n, l) in enumerate([("hex", 37, 4), ("cart", 45, 4), ("scattered", 37, 4)])]
+    ens = rbffd.ensemble_problem(mem, precision=precision)
+    clean = ens.state()
+    ens.run(-1, clean)
+    bad = ens.state()
+    wall = int(np.flatnonzero(np.isin(mem[0].nodes.kind, (1, 2)))[0])
+    bad[wall, :] = float("nan")
+    ens.run(-1, bad)
+    ens.sync()
+    assert not torch.all(torch.isfinite(bad[:mem[0].nodes.n_prog]))
+    for r, m in enumerate(mem[1:], start=1):
+        sl = slice(ens.rec0[r], ens.rec0[r] + m.nodes.n_prog)
+        assert torch.equal(bad[sl], clean[sl]), r
+
+
+def test_coarse_draw_runs_to_900s_finite():
+    """Every member of a seeded draw at 200 and 400 m stays finite to 900 s
+    (the draw skips the Cartesian stencil choices that blow up)."""
+    mem = inp.ensemble_members(48, seed=1, spacings=(200.0, 400.0))
+    ens = rbffd.ensemble_problem(mem, precision=32)
+    U = ens.state()
+    ens.run(-1, U)
+    ens.sync()
+    bad = [r for r, m in enumerate(mem) if not np.all(np.isfinite(ens.member_fields(U, r)[:, :m.nodes.n_prog]))]
+    assert not bad, [(r, mem[r].nodes.h, mem[r].nodes.layout, mem[r].n, mem[r].l) for r in bad]
