@@ -128,13 +128,15 @@ def kernel_source_hash(key=""):
     return h.hexdigest()[:16]
 
 
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+
+
 def profiled_traffic(key, nodes=None, algorithmic=None, **launch):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     the current kernel source and the same launch shape (the ``launch``
     keywords, e.g. threads_per_node, that the summary records); else None."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
-        with open(path) as f:
+        with open(TRAFFIC_JSON) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
