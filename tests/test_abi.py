@@ -50,6 +50,15 @@ def test_argument_errors_need_no_gpu(lib):
     assert rc == rbffd.RBF_E_ARG
     rc = lib.rbf_rk4_step(None, 0.0, 1.0, None)
     assert rc == rbffd.RBF_E_ARG
+    # an ensemble's lanes per node: 0 (autotune), 1, 2 or 4
+    common = rbffd.NSParams(n_sten=37, phs_p=7, poly_l=4, hv_k=3, hv_p=7, precision=32, threads_per_node=3)
+    mem = (rbffd.EnsMember * 1)(rbffd.EnsMember(n_prog=4, n_all=8, n_sten=37, poly_l=4, dt=1.0, n_steps=1))
+    buf = (C.c_double * 8)()
+    ibuf = (C.c_int32 * 8)()
+    h = C.c_void_p()
+    rc = lib.rbf_ens_create(C.byref(h), C.byref(common), 1, mem, buf, buf, ibuf, ibuf, None)
+    assert rc == rbffd.RBF_E_ARG and not h.value
+    assert b"threads per node" in lib.rbf_last_error()
 
 
 def test_struct_layouts_match_header():
