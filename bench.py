@@ -1,21 +1,40 @@
 """Throughput of the PHS RBF-FD hot path on one GB300 (or N replicas).
 
-Workload (default): the density current of Sec. 6.3 on hexagonal nodes at
-100 m -- 38,400 prognostic nodes + 1,024 ghosts, PHS r^7 + degree-4
-polynomials, n = 37, Delta^3 hyperviscosity, mu = 75 m^2/s, dt = 0.25 s --
-stepped in FP32 (FP64-built weights stored in FP32).  One step = one
-classical RK4 step: four stages, each a ghost solve (Sec. 5.2) and one fused
-right-hand-side + RK4-update kernel.  Setup (stencils, weights, packing,
-ghost inverses) is timed separately and reported under "setup".
+Headline workload: the warm rising bubble in a walled [0, 20] x [0, 10] km box
+-- a +2 K cos^2 bubble of radius 2 km at (10, 2) km on a neutral 300 K base
+state, 308,097 quasi-uniform Poisson-disk nodes at 25 m (seed 1) + 2,400
+ghosts, PHS r^9 + degree-5 polynomials, n = 56, Delta^3 hyperviscosity from
+r^9, mu = 10 m^2/s, dt = 1/16 s -- stepped in FP64, the paper's precision.
+One step = one classical RK4 step: four stages, each a ghost solve (Sec. 5.2)
+and one fused right-hand-side + RK4-update kernel, replayed from a CUDA graph.
+Setup (stencils, weights, packing, ghost inverses) is timed separately.
 
 Metric: node-RHS evaluations per second (4 per node per RK4 step).  The
-working set (~31 MB) fits in L2, so L2 is flushed (a 512 MB write) between
-timed steps; each step is timed alone with CUDA events on the problem's
-stream.  The FP64 form of the same workload is reported under "fp64".
+headline's working set (operators, records, RK4 buffers: ~0.7 GB in FP64) is
+several times larger than L2, so steps are timed back to back without an L2
+flush, each with CUDA events on the problem's stream.  The dominant kernel is
+the FP64 stage kernel, bound by the FP64 pipe: its roofline is in TFLOP/s
+against a DGEMM measured in the same run.
+
+Beside the headline, in the same JSON line:
+  bubble_fp32      the same workload with FP64-built weights stored in FP32
+                   and FP32 stages (HBM roofline), and its per-field error at
+                   t = 1000 s against the FP64 run
+  density_current  Sec. 6.3 at hexagonal 100 m (38,400 nodes, n = 37, r^7 +
+                   deg 4): FP32 in one persistent launch per step (L2
+                   flushed between steps), FP64, and FP32's error at 900 s
+  advection        the deformational-flow scalar on 64 x 64 nodes, one period
+  weights          the FP64 weight build of the headline node set
+  roofline_large   the density current at 25 m (608k nodes): the FP32 stage
+                   kernel against HBM, per-node and lattice operator storage
+  batched          256 uneven density-current members in FP32 and FP64, and
+                   the FP32 error at 900 s on a subset
+  learned          the coarse-grid correction against plain runs at a stated
+                   error
 
 --impl reference times the FP64 CPU oracle (the only other implementation of
-the method here) on a bounded sample of the same workload: one 1/8-width strip
-per host core.
+the method here) on a bounded sample of the headline workload: one 1/16-width
+strip of the walled box per host core.
 """
 import argparse
 import hashlib
@@ -33,35 +52,46 @@ sys.path.insert(0, ROOT)
 
 METRIC = "node-RHS evals/s (RK4)"
 UNIT = "node-RHS/s"
-WORKLOAD = "density current (Sec. 6.3), hexagonal 100 m, 38400 nodes + 1024 ghosts, r^7 + deg 4, n=37, Delta^3"
+LEGS = ("headline", "bubble_fp32", "density_current", "advection", "weights", "large", "batched", "learned")
+STRIPS = 16          # the CPU sample: 1/16-width strips of the walled box
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
-    ap.add_argument("--h", type=float, default=100.0)
+    ap.add_argument("--legs", default="all",
+                    help="comma list of " + ",".join(LEGS) + " (default all); the headline always runs")
+    ap.add_argument("--bubble-h", type=float, default=25.0, help="node spacing of the headline bubble (m)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--threads-per-node", type=int, default=0, help="0 = autotuned")
+    ap.add_argument("--no-final-error", action="store_true",
+                    help="skip the whole runs to t_final that state the FP32 forms' errors")
+    ap.add_argument("--h", type=float, default=100.0, help="density-current spacing (m)")
+    ap.add_argument("--threads-per-node", type=int, default=0, help="density current: 0 = autotuned")
     ap.add_argument("--run-mode", default="auto", choices=["auto", "graph", "persistent"],
-                    help="headline run mode (auto: timed at creation); fixing it makes profiled runs reproducible")
+                    help="density current FP32 run mode (auto: timed at creation)")
     ap.add_argument("--persistent-lanes", type=int, default=1, help="lanes per node with --run-mode persistent")
     ap.add_argument("--persistent-ctas", type=int, default=0, help="CTAs with --run-mode persistent (0: one per SM)")
     ap.add_argument("--ens-runs", type=int, default=256, help="ensemble members (0 = skip the batched case)")
     ap.add_argument("--ens-steps", type=int, default=40, help="timed global RK4 steps of the ensemble")
+    ap.add_argument("--ens-final-members", type=int, default=32,
+                    help="members run to 900 s in FP32 and FP64 for the batched error at t_final")
     ap.add_argument("--ens-threads", type=int, default=0, choices=(0, 1, 2, 4),
                     help="lanes per node of the batched ensembles (0 = autotuned)")
-    ap.add_argument("--learned", type=int, default=1, help="1 = measure the learned coarse-grid correction")
     ap.add_argument("--learned-coarse", type=float, default=400.0)
     ap.add_argument("--learned-ratio", type=int, default=4)
     ap.add_argument("--learned-seeds", type=int, default=16)
+    ap.add_argument("--learned-iters", type=int, default=30000)
     ap.add_argument("--large-h", type=float, default=25.0,
-                    help="spacing of the HBM-roofline case (0 = skip); its working set exceeds L2")
-    return ap.parse_args()
+                    help="spacing of the HBM-roofline density current; its working set exceeds L2")
+    a = ap.parse_args()
+    a.legs = set(LEGS) if a.legs == "all" else {"headline"} | {s.strip() for s in a.legs.split(",") if s.strip()}
+    unknown = a.legs - set(LEGS)
+    if unknown:
+        ap.error(f"unknown legs {sorted(unknown)}")
+    return a
 
 
 def dist_env():
@@ -201,7 +231,145 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_problem(h, precision, tpn=0, run_mode="auto", lanes=1, ctas=0):
+def bubble_workload(h):
+    from paper_1509_02615_gb300 import configs
+    return configs.bubble(h=h, seed=1, t_end=1000.0)
+
+
+def headline_config(wl, world):
+    """The headline's config object (the same in both arms)."""
+    nd = wl.nodes
+    return {"workload": f"warm bubble in a walled [0,20]x[0,10] km box, Poisson-disk nodes at {nd.h:g} m "
+                        f"({nd.n_prog} + {nd.n_ghost} ghosts), r^9 + deg 5, n=56, Delta^3 from r^9, mu=10, "
+                        f"dt={wl.dt:g} s",
+            "n_prog": nd.n_prog, "n_ghost": nd.n_ghost, "dt_s": wl.dt, "precision": "fp64",
+            "l2": "not flushed: inputs larger than L2 (~0.7 GB of FP64 operators, records and RK4 buffers)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def time_run(torch, pb, U, t0, dt, n_steps):
+    """Device time (ms) of one rbf_run of n_steps on the current stream."""
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    pb.run(t0, dt, n_steps, U)
+    e1.record(stream)
+    e1.synchronize()
+    pb.sync()
+    return e0.elapsed_time(e1)
+
+
+def rel_fields(a, b):
+    """Per-field relative l2 of field-major arrays [4, n]."""
+    return [float(np.linalg.norm(a[f] - b[f]) / max(np.linalg.norm(b[f]), 1e-300)) for f in range(a.shape[0])]
+
+
+def headline_case(torch, args, wl, world, local, p64):
+    """The headline: FP64 RK4 steps of the bubble, each timed with CUDA
+    events; then the same steps with events around the four stage kernels
+    (the dominant kernel's average launch time); then the end-to-end form on
+    a pinned host state."""
+    from paper_1509_02615_gb300 import rbffd
+    nodes = wl.nodes
+    t0 = time.perf_counter()
+    pb = rbffd.ns_problem(nodes, precision=64, **wl.params)
+    create_s = time.perf_counter() - t0
+    info = pb.info()
+    U = rbffd.state_tensor(wl.U0, 64)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        step_ms, _ = time_steps(torch, pb, U, wl.dt, args.steps, args.warmup, None, False, nvtx="timed")
+        torch.cuda.synchronize()
+    _, stage_ms = time_steps(torch, pb, U, wl.dt, args.steps, 1, None, True)
+    mm = pb.minmax(U)   # fails loudly on NaN/Inf
+    total_ms = max_over_ranks(sum(step_ms), world)
+    value = whole_job_rate(4.0 * nodes.n_prog * args.steps, world, total_ms / 1e3)
+    persistent = info["run_mode"] == 2
+    if persistent:
+        avg_ms = float(np.mean(step_ms))
+        flops = 4.0 * info["rhs_flops_per_node"] * nodes.n_prog
+        kernel, share = "rk4_persistent", 1.0
+    else:
+        avg_ms = float(np.mean(stage_ms)) / 4.0
+        flops = info["rhs_flops_per_node"] * nodes.n_prog
+        kernel, share = "ns_stage_kernel<double>", float(np.sum(stage_ms) / np.sum(step_ms))
+    ach = flops / (avg_ms / 1e3) / 1e12
+    key = f"ns_stage_fp64_bubble{int(nodes.h)}"
+    roof = {"bound": "alu", "achieved": ach, "peak": p64, "unit": "TFLOP/s", "frac": ach / p64,
+            "traffic": None if persistent else profiled_traffic(key, threads_per_node=info["threads_per_node"]),
+            "kernel": kernel, "algorithmic_flops_per_launch": flops,
+            "algorithmic_bytes_per_launch": info["rhs_bytes_per_node"] * nodes.n_prog * (4 if persistent else 1),
+            "avg_launch_ms": avg_ms, "kernel_share_of_step": share,
+            "peak_source": "FP64 DGEMM (cuBLAS via torch.matmul, 4096^3) measured in this run; GB300 nominal FP64 "
+                           "1.25 TFLOP/s", "frac_of_nominal": ach / 1.25,
+            "hbm_GBps": info["rhs_bytes_per_node"] * nodes.n_prog * (4 if persistent else 1) / (avg_ms / 1e3) / 1e9}
+    # end to end through the C ABI: pinned host state -> device, one RK4 step, device -> host
+    Uh = rbffd.state_tensor(wl.U0, 64, device="cpu").pin_memory()
+    n_e2e = max(5, args.steps // 4)
+    pb.run_host(0.0, wl.dt, 1, Uh)
+    t0 = time.perf_counter()
+    for s in range(n_e2e):
+        pb.run_host(s * wl.dt, wl.dt, 1, Uh)
+    e2e_s = time.perf_counter() - t0
+    state_bytes = Uh.numel() * Uh.element_size()
+    e2e = {"value": 4.0 * nodes.n_prog * n_e2e * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
+           "note": "rbf_run_host per RK4 step: pinned host state -> device, one RK4 step, device -> host"}
+    out = {"value": value, "ms_per_step": total_ms / args.steps, "roofline": roof, "clocks": clk.summary(),
+           "e2e": e2e, "gpu_launches": (1 if persistent else info["launches_per_step"]) * args.steps,
+           "launch": {"run_mode": "persistent" if persistent else "graph",
+                      "threads_per_node": info["threads_per_node"], "prefetch": info["prefetch"],
+                      "launches_per_step": info["launches_per_step"]},
+           "setup": {"create_s": create_s, "weight_build_ms": info["weight_build_ms"],
+                     "ghost_setup_ms": info["ghost_setup_ms"]},
+           "state_minmax": {"theta_max": float(mm[2, 1]), "w_min": float(mm[1, 0]), "w_max": float(mm[1, 1])}}
+    return pb, out
+
+
+def bubble_fp32_case(torch, args, wl, pb64, pk, pk_kind):
+    """The headline workload in FP32 (FP64-built weights stored in FP32): its
+    throughput, the stage kernel's HBM roofline, and both precisions run to
+    t = 1000 s: FP32's per-field error against FP64 there, and the time of
+    each whole run."""
+    from paper_1509_02615_gb300 import rbffd
+    nodes = wl.nodes
+    pb = rbffd.ns_problem(nodes, precision=32, **wl.params)
+    info = pb.info()
+    U = rbffd.state_tensor(wl.U0, 32)
+    step_ms, _ = time_steps(torch, pb, U, wl.dt, args.steps, args.warmup, None, False, nvtx="timed_fp32")
+    _, stage_ms = time_steps(torch, pb, U, wl.dt, args.steps, 1, None, True)
+    avg = float(np.mean(stage_ms)) / 4.0
+    bpl = info["rhs_bytes_per_node"] * nodes.n_prog
+    ach = bpl / (avg / 1e3) / 1e9
+    out = {"workload": "the headline workload, FP64-built weights stored in FP32, FP32 stages",
+           "value": 4.0 * nodes.n_prog * args.steps / (float(sum(step_ms)) / 1e3), "unit": UNIT,
+           "ms_per_step": float(sum(step_ms)) / args.steps, "dtype": "f32",
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": ach / pk["hbm_gbs"], "kernel": "ns_stage_kernel<float>",
+                        "traffic": profiled_traffic(f"ns_stage_fp32_bubble{int(nodes.h)}",
+                                                    threads_per_node=info["threads_per_node"]),
+                        "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg,
+                        "kernel_share_of_step": float(np.sum(stage_ms) / np.sum(step_ms)),
+                        "peak_source": f"{pk_kind} hbm_gbs"},
+           "threads_per_node": info["threads_per_node"], "launches_per_step": info["launches_per_step"]}
+    if not args.no_final_error:
+        A32 = rbffd.state_tensor(wl.U0, 32)
+        ms32 = time_run(torch, pb, A32, 0.0, wl.dt, wl.n_steps)
+        A64 = rbffd.state_tensor(wl.U0, 64)
+        ms64 = time_run(torch, pb64, A64, 0.0, wl.dt, wl.n_steps)
+        f32 = rbffd.fields(A32)[:, :nodes.n_prog]
+        f64 = rbffd.fields(A64)[:, :nodes.n_prog]
+        out["error_at_1000s"] = {"fields": ["u", "w", "theta'", "pi'"], "rel_l2_fp32_vs_fp64": rel_fields(f32, f64),
+                                 "steps": wl.n_steps,
+                                 "note": "the FP64 run matches the FP64 oracle (tests); FP32 against it at t_final"}
+        out["time_to_1000s_s"] = {"fp32": ms32 / 1e3, "fp64": ms64 / 1e3, "fp32_speedup": ms64 / ms32}
+    pb.close()
+    return out
+
+
+def make_dc_problem(h, precision, tpn=0, run_mode="auto", lanes=1, ctas=0):
     from paper_1509_02615_gb300 import inputs as inp
     from paper_1509_02615_gb300 import rbffd
     nodes = inp.density_current_nodes(h)
@@ -214,21 +382,160 @@ def make_problem(h, precision, tpn=0, run_mode="auto", lanes=1, ctas=0):
     return nodes, pb, U0
 
 
-def time_steps(torch, pb, U, dt, steps, warmup, flush, stage_timing):
-    """Per-step device times (ms) and summed stage-kernel times (ms)."""
+def density_current_case(torch, args, pk, pk_kind, p64, flush):
+    """Sec. 6.3 at hexagonal 100 m: FP32 (each RK4 step one persistent
+    launch when that is faster, L2 flushed between steps: the working set is
+    ~31 MB), a sustained 400-step run, FP64, and FP32's error at 900 s."""
+    from paper_1509_02615_gb300 import rbffd
+    nodes, pb, U0 = make_dc_problem(args.h, 32, args.threads_per_node, args.run_mode, args.persistent_lanes,
+                                    args.persistent_ctas)
+    info = pb.info()
+    dt = args.h / 400.0
+    U = rbffd.state_tensor(U0, 32)
+    persistent = info["run_mode"] == 2
+    step_ms, _ = time_steps(torch, pb, U, dt, args.steps, args.warmup, flush, False)
+    stage_ms = [] if persistent else time_steps(torch, pb, U, dt, args.steps, 1, flush, True)[1]
+    if persistent:
+        avg_ms, bpl, kernel, share = float(np.mean(step_ms)), 4.0 * info["rhs_bytes_per_node"] * nodes.n_prog, \
+            "rk4_persistent", 1.0
+    else:
+        avg_ms, bpl, kernel = float(np.mean(stage_ms)) / 4.0, info["rhs_bytes_per_node"] * nodes.n_prog, \
+            "ns_stage_kernel<float>"
+        share = float(np.sum(stage_ms) / np.sum(step_ms))
+    ach = bpl / (avg_ms / 1e3) / 1e9
+    key = f"{'persistent' if persistent else 'ns_stage'}_fp32_hex{int(args.h)}"
+    launch = ({"persistent_lanes": info["persist_lanes"], "persistent_ctas": info["persist_ctas"]} if persistent
+              else {"threads_per_node": info["threads_per_node"]})
+    out = {"workload": f"density current (Sec. 6.3), hexagonal {args.h:g} m, {nodes.n_prog} nodes + "
+                       f"{nodes.n_ghost} ghosts, r^7 + deg 4, n=37, Delta^3, mu=75, dt={dt:g} s",
+           "value": 4.0 * nodes.n_prog * args.steps / (float(sum(step_ms)) / 1e3), "unit": UNIT, "dtype": "f32",
+           "ms_per_step": float(sum(step_ms)) / args.steps,
+           "l2": "flushed between timed steps (512 MB write); working set ~31 MB",
+           "run_mode": "persistent" if persistent else "graph", "threads_per_node": info["threads_per_node"],
+           "persistent_lanes": info["persist_lanes"], "persistent_chunk": info["persist_chunk"],
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": ach / pk["hbm_gbs"], "traffic": profiled_traffic(key, **launch), "kernel": kernel,
+                        "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg_ms, "kernel_share_of_step": share,
+                        "peak_source": f"{pk_kind} hbm_gbs",
+                        "note": "the working set fits in L2: latency-bound, reported against HBM for reference"}}
+    # a sustained run (one rbf_run of many steps, L2 flushed once before it)
+    sus = 400
+    flush.zero_()
+    Us = rbffd.state_tensor(U0, 32)
+    sus_ms = time_run(torch, pb, Us, 0.0, dt, sus)
+    out["sustained_run"] = {"value": 4.0 * nodes.n_prog * sus / (sus_ms / 1e3), "unit": UNIT, "steps": sus,
+                            "ms_per_step": sus_ms / sus}
+    n64, pb64, _ = make_dc_problem(args.h, 64)
+    i64 = pb64.info()
+    U64 = rbffd.state_tensor(U0, 64)
+    s64, _ = time_steps(torch, pb64, U64, dt, args.steps, args.warmup, flush, False)
+    t64 = float(sum(s64))
+    if i64["run_mode"] == 2:
+        avg64, flops = t64 / len(s64), 4.0 * i64["rhs_flops_per_node"] * n64.n_prog
+    else:
+        _, k64 = time_steps(torch, pb64, U64, dt, args.steps, 1, flush, True)
+        avg64, flops = float(np.mean(k64)) / 4.0, i64["rhs_flops_per_node"] * n64.n_prog
+    out["fp64"] = {"value": 4.0 * n64.n_prog * len(s64) / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / len(s64),
+                   "run_mode": "persistent" if i64["run_mode"] == 2 else "graph",
+                   "roofline": {"bound": "alu", "achieved": flops / (avg64 / 1e3) / 1e12, "peak": p64,
+                                "unit": "TFLOP/s", "frac": flops / (avg64 / 1e3) / 1e12 / p64,
+                                "peak_source": "measured FP64 DGEMM in this run", "avg_launch_ms": avg64}}
+    if not args.no_final_error:
+        n_end = int(round(900.0 / dt))
+        A64 = rbffd.state_tensor(U0, 64)
+        ms64 = time_run(torch, pb64, A64, 0.0, dt, n_end)
+        A32 = rbffd.state_tensor(U0, 32)
+        ms32 = time_run(torch, pb, A32, 0.0, dt, n_end)
+        f64 = rbffd.fields(A64)[:, :nodes.n_prog]
+        f32 = rbffd.fields(A32)[:, :nodes.n_prog]
+        out["error_at_900s"] = {"fields": ["u", "w", "theta'", "pi'"], "rel_l2_fp32_vs_fp64": rel_fields(f32, f64),
+                                "steps": n_end}
+        out["time_to_900s_s"] = {"fp32": ms32 / 1e3, "fp64": ms64 / 1e3, "fp32_speedup": ms64 / ms32}
+    pb64.close()
+    pb.close()
+    return out
+
+
+def advection_case(torch):
+    """The deformational-flow scalar (64 x 64 nodes, r^7 + deg 4, n = 37,
+    Delta^4 from r^9): one whole period T = 5 (1000 RK4 steps) in FP64 and
+    FP32, after a warm-up period."""
+    from paper_1509_02615_gb300 import configs
+    from paper_1509_02615_gb300 import rbffd
+    wl = configs.advection(64)
+    n = wl.nodes.n_prog
+    out = {"workload": f"scalar advection in the deformational flow, Cartesian 64 x 64 ({n} nodes + reflected "
+                       f"layers), r^7 + deg 4, n=37, Delta^4 from r^9, {wl.n_steps} RK4 steps to t = T"}
+    for prec in (64, 32):
+        pb = rbffd.advection_problem(wl.nodes, precision=prec, **wl.params)
+        P = rbffd.state_tensor(wl.U0, prec)
+        time_run(torch, pb, P, 0.0, wl.dt, wl.n_steps)
+        P = rbffd.state_tensor(wl.U0, prec)
+        ms = time_run(torch, pb, P, 0.0, wl.dt, wl.n_steps)
+        psi = rbffd.fields(P)[0]
+        out[f"fp{prec}"] = {"value": 4.0 * n * wl.n_steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / wl.n_steps,
+                            "return_error_rel_l2": float(np.linalg.norm(psi - wl.U0) / np.linalg.norm(wl.U0))}
+        pb.close()
+    return out
+
+
+def weights_case(torch, nodes, n, p, l, hv_k, peak_tflops, label):
+    """a2 alone: the FP64 weight build of a node set through the C ABI
+    (rbf_build_weights: d/dx, d/dz, Lap, d2/dx2, d2/dz2 and Delta^k, all from
+    r^p with degree l, so one augmented system of size S = n + M per node with
+    K = 6 right-hand sides), timed with CUDA events after a warm-up build.
+    Algorithmic flops per node: (2/3) S^3 + 2 K S^2."""
+    from paper_1509_02615_gb300 import rbffd
+    x = torch.as_tensor(nodes.x, device="cuda")
+    z = torch.as_tensor(nodes.z, device="cuda")
+    idx = rbffd.build_stencils(x, z, nodes.n_prog, n, nodes.period_x)
+    ops = ("dx", "dz", "lap", "dxx", "dzz", "hv")
+    stream = torch.cuda.current_stream()
+
+    def build():
+        rbffd.build_weights(x, z, idx, p, l, ops, hv_k, nodes.period_x)
+
+    build()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    build()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    S = n + (l + 1) * (l + 2) // 2
+    flops = nodes.n_prog * ((2.0 / 3.0) * S ** 3 + 2.0 * len(ops) * S ** 2)
+    ach = flops / (ms / 1e3) / 1e12
+    return {"workload": f"FP64 weights of the {nodes.n_prog} prognostic nodes of {label} (6 operators from r^{p}, "
+                        f"degree {l}, n = {n}: one augmented system of size S = {S} per node)",
+            "ms": ms, "nodes_per_s": nodes.n_prog / (ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": ach / peak_tflops, "algorithmic_flops": flops,
+                         "peak_source": "measured FP64 DGEMM in this run"}}
+
+
+def time_steps(torch, pb, U, dt, steps, warmup, flush, stage_timing, nvtx=None):
+    """Per-step device times (ms) and summed stage-kernel times (ms).  With a
+    ``flush`` buffer, L2 is evicted before every step (for working sets that
+    fit in L2); ``nvtx`` names an NVTX range around the timed steps (for a
+    profiler's launch filter)."""
     stream = torch.cuda.current_stream()
     pb.set_stage_timing(stage_timing)
     t = 0.0
     for _ in range(warmup):
-        flush.zero_()
+        if flush is not None:
+            flush.zero_()
         pb.run(t, dt, 1, U)
         t += dt
     torch.cuda.synchronize()
     step_ms, stage_ms = [], []
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    if nvtx:
+        torch.cuda.nvtx.range_push(nvtx)
     for _ in range(steps):
-        flush.zero_()                    # evict the 31 MB working set from L2
+        if flush is not None:
+            flush.zero_()
         e0.record(stream)
         pb.run(t, dt, 1, U)
         e1.record(stream)
@@ -237,6 +544,8 @@ def time_steps(torch, pb, U, dt, steps, warmup, flush, stage_timing):
         if stage_timing:
             stage_ms.append(pb.stage_kernel_ms())
         t += dt
+    if nvtx:
+        torch.cuda.nvtx.range_pop()
     pb.set_stage_timing(False)
     return step_ms, stage_ms
 
@@ -260,50 +569,12 @@ def fp64_peak_tflops(torch, n=4096, reps=5):
     return 2.0 * n ** 3 / (best / 1e3) / 1e12
 
 
-def weights_case(torch, h, peak_tflops):
-    """a2 alone: the FP64 weight build of the headline node set through the C
-    ABI (rbf_build_weights: d/dx, d/dz, Lap, d2/dx2, d2/dz2 and Delta^3, all
-    from r^7 with degree 4 and n = 37, so one augmented system per node with
-    K = 6 right-hand sides, as rbf_ns_create builds them), timed with CUDA
-    events after a warm-up build.  Algorithmic flops per node:
-    (2/3) S^3 + 2 K S^2 (LU of the S x S system and its K right-hand sides)."""
-    from paper_1509_02615_gb300 import inputs as inp
-    from paper_1509_02615_gb300 import rbffd
-    nodes = inp.density_current_nodes(h)
-    x = torch.as_tensor(nodes.x, device="cuda")
-    z = torch.as_tensor(nodes.z, device="cuda")
-    idx = rbffd.build_stencils(x, z, nodes.n_prog, 37, nodes.period_x)
-    ops = ("dx", "dz", "lap", "dxx", "dzz", "hv")
-    stream = torch.cuda.current_stream()
-
-    def build():
-        rbffd.build_weights(x, z, idx, 7, 4, ops, 3, nodes.period_x)
-
-    build()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    build()
-    e1.record(stream)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    S = 37 + 15
-    flops = nodes.n_prog * ((2.0 / 3.0) * S ** 3 + 2.0 * len(ops) * S ** 2)
-    ach = flops / (ms / 1e3) / 1e12
-    return {"workload": f"FP64 weights of the {nodes.n_prog} prognostic nodes at {h:g} m (6 operators from r^7, "
-                        f"one augmented system of size S = {S} per node)",
-            "ms": ms, "nodes_per_s": nodes.n_prog / (ms / 1e3),
-            "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s",
-                         "frac": ach / peak_tflops, "algorithmic_flops": flops,
-                         "peak_source": "measured cuBLAS DGEMM 4096^3 in this run"}}
-
-
 def large_case(torch, args, flush):
     """The same density current at a finer spacing, whose FP32 working set is
     several times larger than L2: the stage kernel's HBM roofline."""
     from paper_1509_02615_gb300 import rbffd
     pk, pk_kind = peaks()
-    nodes, pb, U0 = make_problem(args.large_h, 32)
+    nodes, pb, U0 = make_dc_problem(args.large_h, 32)
     info = pb.info()
     U = rbffd.state_tensor(U0, 32)
     dt = args.large_h / 400.0
@@ -435,6 +706,8 @@ def ensemble_case(torch, args):
                        for f in range(4)]}
     e64.close()
     del U64, f64
+    if not args.no_final_error and args.ens_final_members > 0:
+        out["error_at_900s"] = ensemble_final_error(torch, members[:args.ens_final_members], args.ens_threads)
     t0 = time.perf_counter()
     lens = rbffd.ensemble_problem(members, precision=32, storage="lattice", threads_per_node=args.ens_threads)
     build_s = time.perf_counter() - t0
@@ -459,6 +732,36 @@ def ensemble_case(torch, args):
     return out
 
 
+def ensemble_final_error(torch, members, threads):
+    """The first members of this rank's share run to t = 900 s (each member
+    to its own step count) in FP32 and in FP64: per-field relative l2 of the
+    concatenated FP32 states against FP64 at t_final, and both run times."""
+    from paper_1509_02615_gb300 import rbffd
+    res = {}
+    for prec in (32, 64):
+        ens = rbffd.ensemble_problem(members, precision=prec, threads_per_node=threads)
+        U = ens.state()
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ens.run(-1, U)
+        e1.record(stream)
+        e1.synchronize()
+        res[prec] = (U.cpu().double(), e0.elapsed_time(e1), ens.node_updates(-1))
+        ens.close()
+        del U
+    (a, ms32, upd), (b, ms64, _) = res[32], res[64]
+    prog = np.concatenate([np.arange(r0, r0 + m.nodes.n_prog) for r0, m in
+                           zip(np.cumsum([0] + [m.nodes.n_all for m in members])[:-1], members)])
+    a, b = a[prog], b[prog]
+    return {"members": len(members), "node_updates": upd,
+            "fields": ["u", "w", "theta'", "pi'"],
+            "rel_l2_fp32_vs_fp64": [float(torch.linalg.vector_norm(a[:, f] - b[:, f]) /
+                                          torch.linalg.vector_norm(b[:, f])) for f in range(4)],
+            "seconds_to_900s": {"fp32": ms32 / 1e3, "fp64": ms64 / 1e3, "fp32_speedup": ms64 / ms32},
+            "finite": bool(torch.isfinite(a).all() and torch.isfinite(b).all())}
+
+
 def learned_case(torch, args):
     """Learned coarse-grid correction: coarse hexagonal runs corrected by the MLP,
     against the restricted fine FP64 reference at 900 s (held-out seeds), with
@@ -473,7 +776,7 @@ def learned_case(torch, args):
     ds = learned.build_dataset(hc, ratio, seeds, 900.0)
     t_data = time.perf_counter() - t0
     t0 = time.perf_counter()
-    mlp, loss = learned.train(ds, n_train, iters=30000, batch=4096, lr=2e-3)
+    mlp, loss = learned.train(ds, n_train, iters=args.learned_iters, batch=4096, lr=2e-3)
     t_train = time.perf_counter() - t0
     alpha, scores = learned.select_alpha(ds, mlp, range(n_train, n_train + n_val))
     test = list(range(n_train + n_val, ns))
@@ -542,18 +845,26 @@ def learned_case(torch, args):
     return out
 
 
-def _oracle_strip(h):
-    """The FP64 oracle on a 1/8-width periodic strip of the workload (same
-    spacing, stencils, operators and boundary treatment), its setup time
-    (stencils, weights, ghost factorisations) and a state one step in."""
-    from oracle.ns import NSOracle
+def _strip_nodes(h, k):
+    """Strip k of the headline's walled box: 1/STRIPS of its width, the same
+    spacing, stencils, operators and walls (Poisson-disk nodes, seed 1 + k),
+    with the warm bubble centred in the strip."""
     from paper_1509_02615_gb300 import inputs as inp
-    width = 25600.0 / 8.0
-    nodes = inp.lattice_nodes("hex", -width, width, 0.0, 6400.0, h, True)
+    width = 20000.0 / STRIPS
+    nodes = inp.poisson_disk_nodes(0.0, width, 0.0, 10000.0, h, seed=1 + k)
+    U = inp.warm_bubble_state(nodes, xc=0.5 * width, R=min(2000.0, 0.4 * width))
+    return nodes, U
+
+
+def _oracle_strip(h, k):
+    """The FP64 oracle on strip k, its setup time (stencils, weights, ghost
+    factorisations) and a state one step in."""
+    from oracle.ns import NSOracle
+    from paper_1509_02615_gb300 import configs
+    nodes, U = _strip_nodes(h, k)
     t0 = time.perf_counter()
-    o = NSOracle(nodes)
+    o = NSOracle(nodes, **configs.BUBBLE_METHOD)
     setup_s = time.perf_counter() - t0
-    U = inp.density_current_state(nodes)
     U = o.rk4_step(0.0, h / 400.0, U)
     return nodes, o, U, setup_s
 
@@ -561,8 +872,8 @@ def _oracle_strip(h):
 def _oracle_rhs_rate(args):
     """RHS evaluations of one strip for budget_s seconds: (evaluations,
     nodes, seconds, setup seconds).  Runs in a spawned worker process."""
-    h, budget_s = args
-    nodes, o, U, setup_s = _oracle_strip(h)
+    h, k, budget_s = args
+    nodes, o, U, setup_s = _oracle_strip(h, k)
     t0 = time.perf_counter()
     n_eval = 0
     while time.perf_counter() - t0 < budget_s:
@@ -571,41 +882,46 @@ def _oracle_rhs_rate(args):
     return n_eval, nodes.n_prog, time.perf_counter() - t0, setup_s
 
 
-def cpu_baseline(h, budget_s=12.0):
-    """FP64 oracle node-RHS/s on the host cores: one strip per core in spawned
-    single-threaded processes (the headline figure), and one core alone."""
+def _spawn_pool_map(fn, jobs):
+    """Map fn over jobs in spawned single-threaded worker processes, one per
+    job, at most one per host core."""
     import multiprocessing as mp
-    n_eval, n_prog, el, setup_s = _oracle_rhs_rate((h, budget_s))
-    single = n_eval * n_prog / el
-    cores = os.cpu_count() or 1
     keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
     saved = {k: os.environ.get(k) for k in keys}
     for k in keys:
-        os.environ[k] = "1"          # the spawned workers' BLAS stays single-threaded
+        os.environ[k] = "1"          # the workers' BLAS stays single-threaded
     try:
-        with mp.get_context("spawn").Pool(cores) as pool:
-            res = pool.map(_oracle_rhs_rate, [(h, budget_s)] * cores)
+        with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+            return pool.map(fn, jobs)
     finally:
         for k, v in saved.items():
             if v is None:
                 os.environ.pop(k, None)
             else:
                 os.environ[k] = v
+
+
+def cpu_baseline(h, budget_s=10.0):
+    """FP64 oracle node-RHS/s on the host cores: one strip per core (up to
+    STRIPS strips) in spawned single-threaded processes."""
+    cores = min(os.cpu_count() or 1, STRIPS)
+    res = _spawn_pool_map(_oracle_rhs_rate, [(h, k, budget_s) for k in range(cores)])
     value = sum(ne * npg / t for ne, npg, t, _ in res)
+    n0, npg0, t_0, setup0 = res[0]
     return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"FP64 oracle RHS (ghost solve + sparse DM products) on periodic strips of the workload, 1/8 of "
-                      f"its width ({n_prog} of 38400 nodes, same h, stencils and walls): one strip per core in "
-                      f"{cores} spawned single-threaded processes, {sum(r[0] for r in res)} evaluations in "
+            "sample": f"FP64 oracle RHS (ghost solves + sparse DM products) on {cores} strips of the workload, each "
+                      f"1/{STRIPS} of its width ({npg0} nodes; same spacing, stencils, operators and walls), one strip "
+                      f"per core in spawned single-threaded processes, {sum(r[0] for r in res)} evaluations in "
                       f"{budget_s:.0f} s each",
-            "single_core": {"value": single, "cores": 1, "evaluations": n_eval, "seconds": el},
-            "oracle_setup_s": setup_s}
+            "single_strip": {"value": n0 * npg0 / t_0, "cores": 1, "evaluations": n0, "seconds": t_0},
+            "oracle_setup_s": setup0}
 
 
 def _oracle_rk4_steps(args):
     """W untimed and K timed oracle RK4 steps on one strip: (nodes, seconds).
     Runs in a spawned worker process."""
-    h, warmup, steps = args
-    nodes, o, U, _ = _oracle_strip(h)
+    h, k, warmup, steps = args
+    nodes, o, U, _ = _oracle_strip(h, k)
     dt = h / 400.0
     for s in range(warmup):
         U = o.rk4_step((1 + s) * dt, dt, U)
@@ -617,43 +933,31 @@ def _oracle_rk4_steps(args):
 
 def run_reference(args, rank, world):
     """The oracle arm: W untimed and K timed RK4 steps of the FP64 oracle on
-    1/8-width strips of the workload (same spacing, stencils, walls), one
-    strip per host core in spawned single-threaded processes; one step is four
-    right-hand sides with their ghost solves.  The rate sums the strips'
-    node-RHS/s."""
+    strips of the headline workload, one strip per host core in spawned
+    single-threaded processes; one step is four right-hand sides with their
+    ghost solves.  The rate sums the strips' node-RHS/s."""
     if rank != 0:
         return
-    import multiprocessing as mp
+    from paper_1509_02615_gb300 import configs
     t_start = time.perf_counter()
-    cores = os.cpu_count() or 1
-    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
-    saved = {k: os.environ.get(k) for k in keys}
-    for k in keys:
-        os.environ[k] = "1"
-    try:
-        with mp.get_context("spawn").Pool(cores) as pool:
-            res = pool.map(_oracle_rk4_steps, [(args.h, args.warmup, args.steps)] * cores)
-    finally:
-        for k, v in saved.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
+    cores = min(os.cpu_count() or 1, STRIPS)
+    res = _spawn_pool_map(_oracle_rk4_steps, [(args.bubble_h, k, args.warmup, args.steps) for k in range(cores)])
     value = sum(4.0 * n * args.steps / el for n, el in res)
     ms_step = 1e3 * float(np.mean([el for _, el in res])) / max(args.steps, 1)
     n_strip = res[0][0]
-    sample = (f"FP64 oracle RK4 steps (ghost solves + sparse DM products) on periodic strips of the workload, 1/8 of "
-              f"its width ({n_strip} of 38400 nodes, same h, stencils and walls), one strip per core in {cores} "
-              f"spawned single-threaded processes: {args.warmup} untimed + {args.steps} timed steps each, "
+    sample = (f"FP64 oracle RK4 steps (ghost solves + sparse DM products) on {cores} strips of the workload, each "
+              f"1/{STRIPS} of its width ({n_strip} nodes; same spacing, stencils, operators and walls), one strip per "
+              f"core in spawned single-threaded processes: {args.warmup} untimed + {args.steps} timed steps each, "
               f"{ms_step:.1f} ms per step per strip")
+    # the config object of the headline (the node set is generated, not solved)
+    wl = configs.bubble(h=args.bubble_h, seed=1, t_end=1000.0)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "fp64 oracle", "l2": "n/a (CPU)",
-                       "sample_nodes": n_strip * cores},
+            "config": headline_config(wl, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": time.perf_counter() - t_start}
+            "sample_nodes": n_strip * cores, "wall_s": time.perf_counter() - t_start}
     print(json.dumps(line), flush=True)
 
 
@@ -674,167 +978,50 @@ def main():
         if rank != 0:
             _build.build()   # no-op once rank 0 has built
     torch.cuda.set_device(local)
-    from paper_1509_02615_gb300 import rbffd
+    from paper_1509_02615_gb300 import inputs as inp
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     pk, pk_kind = peaks()
+    p64 = fp64_peak_tflops(torch)
 
-    nodes, pb, U0 = make_problem(args.h, args.precision, args.threads_per_node, args.run_mode,
-                                 args.persistent_lanes, args.persistent_ctas)
-    info = pb.info()
-    dt = args.h / 400.0
-    U = rbffd.state_tensor(U0, args.precision)
+    wl = bubble_workload(args.bubble_h)
+    pb64, head = headline_case(torch, args, wl, world, local, p64)
+    legs = {}
+    if "bubble_fp32" in args.legs:
+        legs["bubble_fp32"] = bubble_fp32_case(torch, args, wl, pb64, pk, pk_kind)
+    pb64.close()
+    if "weights" in args.legs:
+        legs["weights"] = weights_case(torch, wl.nodes, 56, 9, 5, 3, p64, "the headline bubble")
+        legs["weights"]["density_current_100m"] = weights_case(
+            torch, inp.density_current_nodes(100.0), 37, 7, 4, 3, p64, "the density current at 100 m")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    persistent = info["run_mode"] == 2
-    with ClockSampler(local) as clk:
-        step_ms, _ = time_steps(torch, pb, U, dt, args.steps, args.warmup, flush, False)
-        torch.cuda.synchronize()
-        stage_ms = []
-        if not persistent:
-            # same steps again with timing events around the four stage kernels
-            # (the events also break the programmatic overlap of the launches)
-            _, stage_ms = time_steps(torch, pb, U, dt, args.steps, 1, flush, True)
-    torch.cuda.synchronize()
-    total_ms = max_over_ranks(sum(step_ms), world)
-    value = whole_job_rate(4.0 * nodes.n_prog * args.steps, world, total_ms / 1e3)
-    mm = pb.minmax(U)   # fails loudly on NaN/Inf
-
-    # roofline of the dominant kernel: the persistent kernel (one launch per
-    # step: 4 stages of algorithmic bytes) or the fused RHS + RK4 stage kernel
-    if persistent:
-        avg_ms = float(np.mean(step_ms))
-        bytes_per_launch = 4.0 * info["rhs_bytes_per_node"] * nodes.n_prog
-        kernel = "rk4_persistent"
-        share = 1.0
-    else:
-        avg_ms = float(np.mean(stage_ms)) / 4.0
-        bytes_per_launch = info["rhs_bytes_per_node"] * nodes.n_prog
-        kernel = "ns_stage_kernel"
-        share = float(np.sum(stage_ms) / np.sum(step_ms))
-    achieved = bytes_per_launch / (avg_ms / 1e3) / 1e9
-    key = f"{'persistent' if persistent else 'ns_stage'}_fp{args.precision}_hex{int(args.h)}"
-    roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / pk["hbm_gbs"], "traffic": profiled_traffic(key, **({"persistent_lanes": info["persist_lanes"],
-                                                  "persistent_ctas": info["persist_ctas"]} if persistent else
-                                                 {"threads_per_node": info["threads_per_node"]})),
-            "kernel": kernel,
-            "algorithmic_bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_ms,
-            "kernel_share_of_step": share, "peak_source": f"{pk_kind} hbm_gbs"}
-
-    # context: a sustained run (one rbf_run of many steps, L2 flushed once
-    # before it) -- the way a simulation uses the library; not the headline
-    sus_steps = 400
-    flush.zero_()
-    Us = rbffd.state_tensor(U0, args.precision)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    pb.run(0.0, dt, sus_steps, Us)
-    e1.record(stream)
-    e1.synchronize()
-    pb.sync()
-    sus_ms = e0.elapsed_time(e1)
-    sustained = {"value": 4.0 * nodes.n_prog * sus_steps / (sus_ms / 1e3), "unit": UNIT, "steps": sus_steps,
-                 "ms_per_step": sus_ms / sus_steps,
-                 "note": "one rbf_run of 400 steps, L2 flushed once before it (context only)"}
-
-    # end to end through the C ABI on a pinned host state, copies included
-    Uh = rbffd.state_tensor(U0, args.precision, device="cpu").pin_memory()
-    e2e_steps = max(10, args.steps // 4)
-    pb.run_host(0.0, dt, 1, Uh)
-    t0 = time.perf_counter()
-    for s in range(e2e_steps):
-        pb.run_host(s * dt, dt, 1, Uh)
-    e2e_s = time.perf_counter() - t0
-    state_bytes = Uh.numel() * Uh.element_size()
-    e2e = {"value": 4.0 * nodes.n_prog * e2e_steps * world / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": state_bytes, "d2h_bytes_per_step": state_bytes,
-           "note": "rbf_run_host per RK4 step: pinned host state -> device, one RK4 step, device -> host"}
-
-    fp64 = None
-    weights = None
-    if not args.no_fp64 and args.precision == 32:
-        n64, pb64, _ = make_problem(args.h, 64)
-        U64 = rbffd.state_tensor(U0, 64)
-        i64 = pb64.info()
-        n_t = max(20, args.steps // 4)
-        s64, _ = time_steps(torch, pb64, U64, dt, n_t, args.warmup, flush, False)
-        t64 = float(sum(s64))
-        if i64["run_mode"] == 2:      # one persistent launch per step
-            avg64 = t64 / len(s64)
-            flops = 4.0 * i64["rhs_flops_per_node"] * n64.n_prog
-        else:
-            _, k64 = time_steps(torch, pb64, U64, dt, n_t, 1, flush, True)
-            avg64 = float(np.mean(k64)) / 4.0
-            flops = i64["rhs_flops_per_node"] * n64.n_prog
-        p64 = fp64_peak_tflops(torch)
-        weights = weights_case(torch, args.h, p64)
-        fp64 = {"value": 4.0 * n64.n_prog * len(s64) / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / len(s64),
-                "roofline": {"bound": "alu", "achieved": flops / (avg64 / 1e3) / 1e12, "peak": p64,
-                             "unit": "TFLOP/s", "frac": flops / (avg64 / 1e3) / 1e12 / p64,
-                             "peak_source": "measured cuBLAS DGEMM 4096^3 in this run (nominal GB300 FP64: 1.25)",
-                             "frac_of_nominal": flops / (avg64 / 1e3) / 1e12 / 1.25, "avg_launch_ms": avg64,
-                             "hbm_GBps": i64["rhs_bytes_per_node"] * n64.n_prog / (avg64 / 1e3) / 1e9},
-                "threads_per_node": i64["threads_per_node"],
-                "run_mode": "persistent" if i64["run_mode"] == 2 else "graph",
-                "persistent_lanes": i64["persist_lanes"], "persistent_ctas": i64["persist_ctas"]}
-        # accuracy of the FP32 form: the whole run to 900 s in both precisions
-        # (the FP64 path matches the FP64 oracle to ~1e-12), per-field
-        # relative l2 of FP32 against FP64 at t_final
-        n_end = int(round(900.0 / dt))
-        A64 = rbffd.state_tensor(U0, 64)
-        pb64.run(0.0, dt, n_end, A64)
-        pb64.sync()
-        A32 = rbffd.state_tensor(U0, 32)
-        pb.run(0.0, dt, n_end, A32)
-        pb.sync()
-        f64 = rbffd.fields(A64)[:, :nodes.n_prog]
-        f32 = rbffd.fields(A32)[:, :nodes.n_prog]
-        fp64["fp32_error_at_900s"] = {
-            "fields": ["u", "w", "theta'", "pi'"],
-            "rel_l2_vs_fp64": [float(np.linalg.norm(f32[f] - f64[f]) / np.linalg.norm(f64[f])) for f in range(4)],
-            "steps": n_end}
-        pb64.close()
-
-    large = None
-    if args.large_h > 0:
-        large = large_case(torch, args, flush)
-    batched = None
-    if args.ens_runs > 0:
-        batched = ensemble_case(torch, args)
-    learned_form = None
-    if args.learned:
-        learned_form = learned_case(torch, args)
+    if "density_current" in args.legs:
+        legs["density_current"] = density_current_case(torch, args, pk, pk_kind, p64, flush)
+    if "advection" in args.legs:
+        legs["advection"] = advection_case(torch)
+    if "large" in args.legs and args.large_h > 0:
+        legs["roofline_large"] = large_case(torch, args, flush)
+    del flush
+    if "batched" in args.legs and args.ens_runs > 0:
+        legs["batched"] = ensemble_case(torch, args)
+    if "learned" in args.legs:
+        legs["learned"] = learned_case(torch, args)
 
     base = None
     if rank == 0 and not args.no_cpu_baseline:
-        base = cpu_baseline(args.h)
+        base = cpu_baseline(args.bubble_h)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
-                "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n_prog": nodes.n_prog, "n_ghost": nodes.n_ghost,
-                           "dt_s": dt, "precision": f"fp{args.precision}",
-                           "l2": "flushed between timed steps (512 MB write); working set ~31 MB",
-                           "parallelism": "replicas" if world > 1 else "single GPU",
-                           "threads_per_node": info["threads_per_node"], "prefetch": info["prefetch"],
-                           "run_mode": "persistent" if persistent else "graph",
-                           "persistent_lanes": info["persist_lanes"], "persistent_chunk": info["persist_chunk"]},
-                "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
-                "gpu_launches": (1 if persistent else info["launches_per_step"]) * args.steps,
-                "setup": {"weight_build_ms": info["weight_build_ms"], "ghost_setup_ms": info["ghost_setup_ms"]},
-                "sustained_run": sustained,
-                "fp64": fp64, "weights": weights, "roofline_large": large, "batched": batched,
-                "learned": learned_form,
-                "cpu_baseline": base,
-                "state_minmax": {"theta_min": mm[2, 0], "w_min": mm[1, 0], "w_max": mm[1, 1]}}
+        line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": headline_config(wl, world),
+                "roofline": head["roofline"], "clocks": head["clocks"], "e2e": head["e2e"],
+                "gpu_launches": head["gpu_launches"], "launch": head["launch"], "setup": head["setup"],
+                "state_minmax": head["state_minmax"], "fp64_dgemm_tflops": p64,
+                "cpu_baseline": base}
+        line.update(legs)
         print(json.dumps(line), flush=True)
-    pb.close()
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()

@@ -39,12 +39,15 @@ def vortex_velocity(x, y, t, T):
 
 class AdvectionOracle:
     def __init__(self, nodes, n=37, p=7, l=4, hv_k=4, hv_p=9, gamma_c=2.0 ** -14, gamma=None, T=5.0,
-                 flow="deformational"):
+                 flow="deformational", stencil_order="nearest"):
+        """``stencil_order`` "reversed" lists each stencil's neighbours
+        farthest first (the same method up to rounding)."""
         self.nodes = nodes
         self.n_prog = nodes.n_prog
         self.T = T
         self.flow = flow
-        self.disc = Discretisation(nodes, n, p, l, ops=("dx", "dz"), hv_k=hv_k, hv_p=hv_p)
+        self.disc = Discretisation(nodes, n, p, l, ops=("dx", "dz"), hv_k=hv_k, hv_p=hv_p,
+                                   stencil_order=stencil_order)
         if gamma is None:
             gamma = gamma_c * nodes.h ** (2 * hv_k - 1)
         self.gamma = gamma

@@ -34,10 +34,14 @@ BC_OPS = {"tb": ("dz", "dzz", "dz", "dz"), "lr": ("dxx", "dx", "dx", "dx")}
 
 class NSOracle:
     def __init__(self, nodes, n=37, p=7, l=4, hv_k=3, hv_p=None, mu=75.0, gamma_c=2.0 ** -6,
-                 gamma=None, theta_bar=inp.THETA_BAR):
+                 gamma=None, theta_bar=inp.THETA_BAR, stencil_order="nearest", workers=1):
+        """``stencil_order`` "reversed" lists each stencil's neighbours
+        farthest first (the same method up to rounding: the oracle's own
+        spread); ``workers`` > 1 solves the weights in that many processes."""
         self.nodes = nodes
         self.n_prog = nodes.n_prog
-        self.disc = Discretisation(nodes, n, p, l, ops=("dx", "dz", "lap", "dxx", "dzz"), hv_k=hv_k, hv_p=hv_p)
+        self.disc = Discretisation(nodes, n, p, l, ops=("dx", "dz", "lap", "dxx", "dzz"), hv_k=hv_k, hv_p=hv_p,
+                                   stencil_order=stencil_order, workers=workers)
         self.D = self.disc.D
         self.mu = mu
         self.hv_k = hv_k

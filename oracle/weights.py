@@ -140,3 +140,25 @@ def condition_number(x, z, sten, p, l, period_x=0.0):
     """2-norm condition number of the scaled augmented matrix of one stencil."""
     A = _systems(np.asarray(x, np.float64), np.asarray(z, np.float64), np.asarray(sten)[None, :], p, l, period_x)[0]
     return float(np.linalg.cond(A[0]))
+
+
+def _weights_block(args):
+    return all_weights(*args)
+
+
+def all_weights_pool(x, z, idx, p, l, ops, k=0, period_x=0.0, workers=1):
+    """``all_weights`` over contiguous blocks of stencil rows, one block at a
+    time per worker process (spawned, so that a parent holding a CUDA context
+    is safe).  Every stencil is solved on its own, so the result is the
+    serial one, bit for bit; only the wall time changes."""
+    idx = np.asarray(idx)
+    if workers <= 1 or idx.shape[0] < 4096:
+        return all_weights(x, z, idx, p, l, ops, k, period_x)
+    import multiprocessing as mp
+    x = np.asarray(x, np.float64)
+    z = np.asarray(z, np.float64)
+    cuts = np.linspace(0, idx.shape[0], 4 * workers + 1).astype(np.int64)
+    jobs = [(x, z, idx[a:b], p, l, list(ops), k, period_x) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        parts = pool.map(_weights_block, jobs)
+    return np.concatenate(parts, axis=1)

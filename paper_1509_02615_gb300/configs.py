@@ -62,12 +62,13 @@ def density_current(h: float = 100.0, layout: str = "hex") -> Workload:
 # scattered walled node set has a linear mode outside RK4's stability region
 # (|R| = 1.009 per step at 500 m); c = 2^-4 damps it (|R| <= 1.00003).
 BUBBLE_GAMMA_C = 2.0 ** -4
+BUBBLE_METHOD = dict(n=56, p=9, l=5, hv_k=3, hv_p=9, mu=10.0, gamma_c=BUBBLE_GAMMA_C)
 
 
 def bubble(h: float = 25.0, seed: int = 1, t_end: float = 1000.0) -> Workload:
     nodes = inp.poisson_disk_nodes(0.0, 20000.0, 0.0, 10000.0, h, seed=seed)
-    return Workload("bubble", nodes, dict(n=56, p=9, l=5, hv_k=3, hv_p=9, mu=10.0, gamma_c=BUBBLE_GAMMA_C),
-                    inp.warm_bubble_state(nodes), h / 400.0, int(round(t_end * 400.0 / h)))
+    return Workload("bubble", nodes, dict(BUBBLE_METHOD), inp.warm_bubble_state(nodes), h / 400.0,
+                    int(round(t_end * 400.0 / h)))
 
 
 def translating(h: float = 100.0, layout: str = "hex") -> Workload:

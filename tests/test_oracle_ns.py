@@ -185,3 +185,80 @@ def test_manufactured_rhs_converges_at_polynomial_order(layout):
     slopes = [np.polyfit(np.log(hs), np.log(errs[:, f]), 1)[0] for f in range(4)]
     print(layout, "max-norm errors", errs.tolist(), "orders", slopes)
     assert min(slopes) > 4 - 0.5, (slopes, errs)
+
+
+def _manufactured_laplacians(x, z):
+    """Analytic Laplacians of the first three manufactured fields."""
+    L, H = 51200.0, 6400.0
+    kx, kz = 4.0 * np.pi / L, np.pi / H
+    U0, W0, T0 = 10.0, 5.0, 2.0
+    c, s = np.cos(kx * x), np.sin(kx * x)
+    cz, sz = np.cos(kz * z), np.sin(kz * z)
+    k2 = kx * kx + kz * kz
+    return (-k2 * U0 * c * cz, -k2 * W0 * s * sz,
+            T0 * c * (-kx * kx * sz ** 2 + 2.0 * kz * kz * np.cos(2.0 * kz * z)))
+
+
+@pytest.mark.parametrize("layout", ["hex", "cart"])
+def test_viscous_term_converges_to_the_analytic_laplacian(layout):
+    """Eqs. (uEq)-(thetaEq) carry mu Lap on u, w and theta' and none on pi'
+    (Eq. piEq).  The part of the oracle's right-hand side that mu adds --
+    rhs(mu) - rhs(0) for the same manufactured state, which satisfies the wall
+    conditions of Sec. 6.3 -- must be exactly 0 for pi', and converge to
+    mu Lap f of the analytic fields for u, w, theta' at the order of a
+    second derivative with degree-l polynomials, l - 1 (Sec. 4), with w held
+    at the walls.  A dropped, mis-signed or misplaced viscous term fails it."""
+    mu = 75.0
+    hs = [800.0, 400.0, 200.0]
+    errs = []
+    for h in hs:
+        nodes = inp.density_current_nodes(h, layout=layout)
+        o = NSOracle(nodes, mu=mu, hv_k=0)
+        (u, w, th, pi), _ = _manufactured(nodes.x, nodes.z)
+        U = np.stack([u, w, th, pi])
+        U[:, nodes.n_prog:] = 0.0
+        with_mu = o.rhs(0.0, U)
+        o.mu = 0.0
+        without = o.rhs(0.0, U)
+        visc = with_mu - without
+        assert np.all(visc[3] == 0.0)
+        P = nodes.n_prog
+        lap = [v[:P] for v in _manufactured_laplacians(nodes.x, nodes.z)]
+        exact = np.stack([mu * lap[0], np.where(o.w_dirichlet, 0.0, mu * lap[1]), mu * lap[2]])
+        errs.append([np.abs(visc[f] - exact[f]).max() / np.abs(exact[f]).max() for f in range(3)])
+    errs = np.array(errs)
+    slopes = [np.polyfit(np.log(hs), np.log(errs[:, f]), 1)[0] for f in range(3)]
+    print(layout, "viscous-term max-norm errors", errs.tolist(), "orders", slopes)
+    assert errs[-1].max() < 1e-2, errs
+    assert min(slopes) > (4 - 1) - 0.5, (slopes, errs)
+
+
+def test_hyperviscosity_is_the_same_damping_term_on_every_field(dc800):
+    """Sec. 5.3 adds (-1)^(k+1) gamma Delta^k to every governing equation:
+    with the same input in all four fields, the part of the right-hand side
+    that gamma adds is the same for u, w, theta' and pi' at every node whose
+    stencil reads no ghost (the ghosts follow each field's own wall
+    condition), and it is linear in gamma.  Its sign (damping) is pinned by
+    the linear stability test above, which fails with the opposite sign."""
+    nodes, o = dc800
+    rng = np.random.default_rng(4)
+    scale = np.array([[1.0], [1.0], [1e-3], [1e-6]])
+    U = np.stack([rng.normal(size=nodes.n_all)] * 4) * scale
+    g0 = o.hv_coef
+    base = o.rhs(0.0, U)
+    try:
+        o.hv_coef = 0.0
+        plain = o.rhs(0.0, U)
+        o.hv_coef = 2.0 * g0
+        double = o.rhs(0.0, U)
+    finally:
+        o.hv_coef = g0
+    hv = (base - plain) / scale
+    clean = np.all(o.disc.idx < nodes.n_prog, axis=1)
+    assert clean.sum() >= 200
+    ref = hv[0][clean]
+    tol = 1e-12 * np.abs(ref).max()
+    assert np.abs(ref).max() > 0.0
+    for fld in (1, 2, 3):
+        assert np.allclose(hv[fld][clean], ref, rtol=1e-9, atol=tol), fld
+    assert np.allclose(((double - plain) / scale)[:, clean], 2.0 * hv[:, clean], rtol=1e-9, atol=tol)

@@ -245,3 +245,58 @@ def test_hv_recursion_matches_repeated_laplacian_of_phs():
         assert abs(got - p * p * r ** (p - 2)) < 1e-13 * p * p
         got3 = wt.phs_applied("hv", p, 2, np.array([x]), np.array([z]))[0]
         assert abs(got3 - p * p * (p - 2) ** 2 * r ** (p - 4)) < 1e-12 * p ** 4
+
+
+def _mp_global_interpolant(xs, zs, f, p, l, mp):
+    """The global PHS + degree-l interpolant of f on the nodes, solved and
+    evaluated in 60-digit arithmetic (mpmath); returns s(x, z) and the
+    centre node (the first node)."""
+    n = len(xs)
+    mono = [(d - b, b) for d in range(l + 1) for b in range(d + 1)]
+    X = [mp.mpf(float(v)) for v in xs]
+    Z = [mp.mpf(float(v)) for v in zs]
+    A = mp.matrix(n + len(mono), n + len(mono))
+    for i in range(n):
+        for j in range(n):
+            A[i, j] = mp.sqrt((X[i] - X[j]) ** 2 + (Z[i] - Z[j]) ** 2) ** p
+        for c, (a, b) in enumerate(mono):
+            A[i, n + c] = A[n + c, i] = X[i] ** a * Z[i] ** b
+    coef = mp.lu_solve(A, mp.matrix([mp.mpf(float(v)) for v in f] + [0] * len(mono)))
+
+    def s(x, z):
+        v = sum(coef[j] * mp.sqrt((x - X[j]) ** 2 + (z - Z[j]) ** 2) ** p for j in range(n))
+        return v + sum(coef[n + c] * x ** a * z ** b for c, (a, b) in enumerate(mono))
+
+    return s, X[0], Z[0]
+
+
+@pytest.mark.parametrize("p,l,n_nodes", [(3, 1, 10), (5, 2, 10), (7, 2, 10), (7, 3, 20), (9, 4, 20)])
+def test_every_operator_equals_the_global_interpolants_derivative(p, l, n_nodes):
+    """Brute force for every operator of Eq. (weights), including the second
+    derivatives behind the wall conditions and Delta^k (Sec. 5.3): on small
+    node sets the stencil is the whole set, so w . f must equal L applied to
+    the global interpolant of f at the centre.  The interpolant is solved in
+    60-digit arithmetic and differentiated by central differences of step
+    1e-15 there (the PHS term of the centre node is C^(p-1), so the
+    differences stay exact to far below FP64); Delta^k is the sum of
+    C(k, i) d^2i/dx^2i d^2(k-i)/dz^2(k-i)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    rng = np.random.default_rng(100 * p + l)
+    xs, zs, f = rng.uniform(-1, 1, n_nodes), rng.uniform(-1, 1, n_nodes), rng.normal(size=n_nodes)
+    s, xc, zc = _mp_global_interpolant(xs, zs, f, p, l, mp)
+    step = mp.mpf(10) ** -15
+    dd = lambda a, b: float(mp.diff(s, (xc, zc), (a, b), h=step))
+    exact = {"dx": dd(1, 0), "dz": dd(0, 1), "dxx": dd(2, 0), "dzz": dd(0, 2)}
+    exact["lap"] = exact["dxx"] + exact["dzz"]
+    idx = np.arange(n_nodes)[None, :]
+    ops = ["dx", "dz", "dxx", "dzz", "lap"]
+    W = wt.all_weights(xs, zs, idx, p, l, ops, 0, 0.0)[:, 0, :]
+    for o, op in enumerate(ops):
+        assert abs(W[o] @ f - exact[op]) <= 1e-10 * np.abs(W[o] * f).sum(), (op, W[o] @ f, exact[op])
+    for k in (1, 2, 3):
+        if p < 2 * k + 1:       # Delta^k r^p is singular at the centre (Sec. 5.3: p >= 2k + 1)
+            continue
+        lapk = sum(math.comb(k, i) * dd(2 * i, 2 * (k - i)) for i in range(k + 1))
+        Wh = wt.all_weights(xs, zs, idx, p, l, ["hv"], k, 0.0)[0, 0]
+        assert abs(Wh @ f - lapk) <= 1e-10 * np.abs(Wh * f).sum(), (k, Wh @ f, lapk)
