@@ -69,7 +69,7 @@ const char *rbf_last_error(void);
  *   x, z      device, double [n_all]
  *   idx       device, int32 [n_centers][n] (output; idx[c][0] == c)
  * Errors: RBF_E_ARG for n < 1, n > n_all, n > 128, non-finite coordinates or
- * a node density so uneven that a search window holds > 4096 candidates.
+ * a node density so uneven that a search window holds > 2048 candidates.
  */
 int rbf_build_stencils(const double *x, const double *z, int64_t n_all, int64_t n_centers,
                        int32_t n, double period_x, int32_t *idx, void *stream);
@@ -87,9 +87,10 @@ int rbf_build_stencils(const double *x, const double *z, int64_t n_all, int64_t 
  * rbf_build_stencils; the caller still provides x, z and idx.
  *   Limits: n_all <= 262144 nodes and a binning grid of <= 262144 cells
  *   (about n_all / 2); larger inputs return RBF_E_ARG with a message.
- *   Set-up: the first call on each device looks up the array's device
- *   address (cudaGetSymbolAddress) with that device current; make that first
- *   call before any stream capture.
+ *   Set-up: every call looks up the array's device address
+ *   (cudaGetSymbolAddress) on the current device, so the address stays valid
+ *   across a device reset or a new context; the first call on a device also
+ *   loads the library's device code there.
  *   Sharing: every call on a device uses the same array.  Calls whose work
  *   overlaps on the GPU (other streams or threads) race; serialise them.
  *   Counters are cleared at the start of every call.
@@ -113,6 +114,18 @@ int rbf_build_stencils_static(const double *x, const double *z, int64_t n_all, i
 int rbf_build_weights(const double *x, const double *z, int64_t n_all, const int32_t *idx,
                       int64_t n_centers, int32_t n, double period_x, int32_t p, int32_t l,
                       int32_t hv_k, const int32_t *ops, int32_t n_ops, double *w, void *stream);
+
+/*
+ * Hyperviscosity coefficient of Sec. 5.3 (host only, no GPU needed).  The
+ * paper asks for one constant c "regardless of the resolution" and prints
+ * gamma = c h^(-2k), which cannot be dimensionally right; this library reads
+ * it as gamma = c h^(2k - 1): with dt proportional to h (the paper's time
+ * steps), dt * gamma * rho(Delta^k) is then the same at every resolution.
+ * The term added to the right-hand side is (-1)^(k+1) gamma Delta^k, which
+ * damps.  *gamma = c * h^(2k - 1).
+ * Errors: RBF_E_ARG for c < 0, h <= 0, k < 1 or a null output.
+ */
+int rbf_hyperviscosity_gamma(double c, double h, int32_t k, double *gamma);
 
 /* ---- problems: a stepping context built once, stepped many times -------- */
 typedef struct rbf_problem rbf_problem;
@@ -139,9 +152,15 @@ typedef struct rbf_ns_params {
                            the only way to choose it for an ensemble         */
     double period_x;    /* > 0: periodic in x with this period (m)            */
     double mu;          /* viscosity (m^2/s)                                  */
-    double gamma;       /* hyperviscosity coefficient gamma >= 0              */
+    double gamma;       /* hyperviscosity coefficient gamma >= 0, used as
+                           given when gamma_c = 0                            */
     double theta_bar;   /* background potential temperature T_s (300 K)      */
     double g, cp, cv, rd; /* 9.81, 1004, 717, 287                             */
+    double gamma_c;     /* > 0: the library forms gamma = gamma_c *
+                           spacing^(2 hv_k - 1) (rbf_hyperviscosity_gamma;
+                           gamma must then be 0); 0: gamma as given          */
+    double spacing;     /* node spacing h in the case's length unit (m) for
+                           gamma_c; ensembles take it per member             */
 } rbf_ns_params;
 
 /*
@@ -169,8 +188,10 @@ typedef struct rbf_adv_params {
     int32_t hv_k;       /* 4                                                  */
     int32_t hv_p;       /* 9 (Delta^4 r^7 is singular at r = 0)               */
     int32_t precision;  /* 64 or 32                                           */
-    double gamma;       /* hyperviscosity coefficient                        */
+    double gamma;       /* hyperviscosity coefficient (used when gamma_c = 0) */
     double period_T;    /* velocity time factor cos(pi t / T)                 */
+    double gamma_c;     /* > 0: gamma = gamma_c * spacing^(2 hv_k - 1)        */
+    double spacing;     /* node spacing h (unit square: 1 / (m - 1))          */
 } rbf_adv_params;
 
 /*
@@ -220,9 +241,11 @@ typedef struct rbf_ens_member {
     int32_t n_sten;         /* its stencil size                                   */
     int32_t poly_l;         /* its polynomial degree                              */
     double period_x;        /* > 0: periodic in x                                 */
-    double gamma;           /* its hyperviscosity coefficient                     */
+    double gamma;           /* its hyperviscosity coefficient (common.gamma_c = 0) */
     double dt;              /* its RK4 time step                                  */
     int64_t n_steps;        /* steps to its end time                              */
+    double spacing;         /* its node spacing h: with common.gamma_c > 0 its
+                               gamma is common.gamma_c * spacing^(2 hv_k - 1)    */
 } rbf_ens_member;
 
 /*

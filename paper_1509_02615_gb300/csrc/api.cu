@@ -284,6 +284,17 @@ void choose_run_mode(Problem &pb, int mode, int lanes, int ctas) {
 
 }  // namespace
 
+// Hyperviscosity coefficient of a problem (Sec. 5.3): gamma_c > 0 forms
+// gamma = gamma_c h^(2k - 1) (the reading of the paper's resolution-independent
+// constant; see rbf_hyperviscosity_gamma); gamma_c == 0 takes gamma as given.
+double resolve_gamma(double gamma, double gamma_c, double spacing, int hv_k) {
+    RBF_REQUIRE(std::isfinite(gamma_c) && gamma_c >= 0.0, "gamma_c must be >= 0");
+    if (gamma_c == 0.0 || hv_k < 1) return gamma;
+    RBF_REQUIRE(gamma == 0.0, "give either gamma or gamma_c, not both");
+    RBF_REQUIRE(std::isfinite(spacing) && spacing > 0.0, "gamma_c needs a node spacing > 0");
+    return gamma_c * std::pow(spacing, 2 * hv_k - 1);
+}
+
 // Builds a Navier-Stokes problem (stencils, weights, packing, ghost systems).
 // with_scratch = false leaves out the RK4 stage buffers (ensemble members
 // step in their ensemble's buffers).
@@ -294,6 +305,7 @@ void build_ns(Problem &pb, const rbf_ns_params &prm, const double *x, const doub
     RBF_REQUIRE(prm.precision == 64 || prm.precision == 32, "precision must be 64 or 32");
     RBF_REQUIRE(prm.n_sten >= 2, "stencil size must be >= 2");
     RBF_REQUIRE(prm.mu >= 0.0 && prm.gamma >= 0.0, "mu and gamma must be >= 0");
+    const double gamma = resolve_gamma(prm.gamma, prm.gamma_c, prm.spacing, prm.hv_k);
     RBF_REQUIRE(prm.theta_bar > 0.0 && prm.cp > 0.0 && prm.cv > 0.0, "bad physical constants");
     RBF_REQUIRE(kind != nullptr, "null kind");
     RBF_REQUIRE(n_all == n_prog || ghost_owner != nullptr, "ghosts need ghost_owner");
@@ -309,8 +321,8 @@ void build_ns(Problem &pb, const rbf_ns_params &prm, const double *x, const doub
     pb.hv_p = prm.hv_p;
     pb.period_x = prm.period_x;
     pb.mu = prm.mu;
-    pb.gamma = prm.gamma;
-    pb.hvc = prm.hv_k > 0 ? ((prm.hv_k % 2 == 1) ? 1.0 : -1.0) * prm.gamma : 0.0;  // (-1)^(k+1) gamma
+    pb.gamma = gamma;
+    pb.hvc = prm.hv_k > 0 ? ((prm.hv_k % 2 == 1) ? 1.0 : -1.0) * gamma : 0.0;  // (-1)^(k+1) gamma
     pb.theta_bar = prm.theta_bar;
     pb.g = prm.g;
     pb.cp = prm.cp;
@@ -415,6 +427,7 @@ int rbf_adv_create_flow(rbf_problem **out, const rbf_adv_params *prm, const doub
                         "flow part %d has a non-finite coefficient", k);
         RBF_REQUIRE(prm->precision == 64 || prm->precision == 32, "precision must be 64 or 32");
         RBF_REQUIRE(prm->period_T > 0.0 && prm->gamma >= 0.0, "period_T must be > 0 and gamma >= 0");
+        const double gamma = rbf::resolve_gamma(prm->gamma, prm->gamma_c, prm->spacing, prm->hv_k);
         for (int64_t j = 0; j < n_all; ++j)
             RBF_REQUIRE(src[j] >= 0 && src[j] < n_prog && (j >= n_prog || src[j] == j),
                         "src[%lld]=%d invalid", (long long)j, src[j]);
@@ -430,8 +443,8 @@ int rbf_adv_create_flow(rbf_problem **out, const rbf_adv_params *prm, const doub
             pb.l = prm->poly_l;
             pb.hv_k = prm->hv_k;
             pb.hv_p = prm->hv_p;
-            pb.gamma = prm->gamma;
-            pb.hvc = prm->hv_k > 0 ? ((prm->hv_k % 2 == 1) ? 1.0 : -1.0) * prm->gamma : 0.0;
+            pb.gamma = gamma;
+            pb.hvc = prm->hv_k > 0 ? ((prm->hv_k % 2 == 1) ? 1.0 : -1.0) * gamma : 0.0;
             pb.period_T = prm->period_T;
             pb.diff = 0;
             pb.n_vparts = n_parts;
@@ -692,3 +705,13 @@ int rbf_stage_kernel_ms(rbf_problem *h, double *ms) {
 }
 
 }  // extern "C"
+
+int rbf_hyperviscosity_gamma(double c, double h, int32_t k, double *gamma) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(gamma, "null output");
+        RBF_REQUIRE(std::isfinite(c) && c >= 0.0, "c must be >= 0");
+        RBF_REQUIRE(std::isfinite(h) && h > 0.0, "h must be > 0");
+        RBF_REQUIRE(k >= 1, "k must be >= 1");
+        *gamma = c * std::pow(h, 2 * k - 1);
+    });
+}

@@ -450,7 +450,10 @@ void build_ensemble(Problem &pb, const rbf_ns_params &common, int n, const rbf_e
         p.n_sten = mr.n_sten;
         p.poly_l = mr.poly_l;
         p.period_x = mr.period_x;
-        p.gamma = mr.gamma;
+        // each member's own gamma: common.gamma_c with the member's spacing,
+        // or the member's gamma as given
+        p.gamma = resolve_gamma(mr.gamma, common.gamma_c, mr.spacing, common.hv_k);
+        p.gamma_c = 0.0;
         p.threads_per_node = 2;
         std::unique_ptr<Problem> m(new Problem());
         build_ns(*m, p, x + off_all, z + off_all, mr.n_prog, mr.n_all, kind + off_prog, owner + off_ghost, stream,

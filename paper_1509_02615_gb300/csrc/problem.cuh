@@ -173,6 +173,8 @@ void autotune_threads_per_node(Problem &pb);
 void pack_operators(Problem &pb);
 void pack_lattice(Problem &pb, const std::vector<double> &comb, int nops);
 double ns_rhs_bytes(const Problem &pb);
+// gamma of Sec. 5.3 from a problem's gamma or (gamma_c, spacing) (api.cu)
+double resolve_gamma(double gamma, double gamma_c, double spacing, int hv_k);
 int32_t lattice_classes(const int32_t *idx, const double *x, const double *z, int64_t n_prog, int n,
                         double period_x, double h, int min_members, int32_t *cls);
 void build_ghost_plan(Problem &pb, const int32_t *kind_host, const int32_t *owner_host);

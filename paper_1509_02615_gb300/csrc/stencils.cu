@@ -10,7 +10,6 @@
 // brute-force sort over all nodes.
 #include <cfloat>
 #include <cmath>
-#include <mutex>
 
 #include "common.cuh"
 
@@ -308,23 +307,15 @@ constexpr size_t kStaticScratchBytes = kOffStart + align256((kStaticMaxCells + 1
 
 static __device__ __align__(256) unsigned char g_stencil_scratch[kStaticScratchBytes];
 
-std::mutex g_scratch_mu;
-unsigned char *g_scratch_addr[256] = {};
-
 // Device address of the scratch array on the current device.  In host code
-// the symbol is only a stand-in, so the address is looked up once per device
-// with that device current and cached.
+// the symbol is only a stand-in, so the address is looked up with the device
+// current -- on every call, not cached: after a device reset or in a new
+// context the module is loaded again and the array moves.  The lookup is
+// cheap next to the call's own two stream synchronisations.
 unsigned char *static_scratch() {
-    int dev = 0;
-    RBF_CUDA(cudaGetDevice(&dev));
-    RBF_REQUIRE(dev >= 0 && dev < 256, "device ordinal %d out of range", dev);
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
-        void *ptr = nullptr;
-        RBF_CUDA(cudaGetSymbolAddress(&ptr, g_stencil_scratch));
-        g_scratch_addr[dev] = static_cast<unsigned char *>(ptr);
-    }
-    return g_scratch_addr[dev];
+    void *ptr = nullptr;
+    RBF_CUDA(cudaGetSymbolAddress(&ptr, g_stencil_scratch));
+    return static_cast<unsigned char *>(ptr);
 }
 
 }  // namespace

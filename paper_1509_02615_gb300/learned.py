@@ -1,6 +1,7 @@
 """Learned coarse-grid correction workflow (a9).
 
-The training data are fine runs of the method, restricted (injection) to
+The training data are fine runs of the method, restricted (a Gaussian average
+over one coarse spacing by default, or injection) to
 the nodes of a nested coarse lattice.  Each training sample pairs a coarse
 state with the tendency that one coarse RK4 step misses:
     target = (R u_fine(t + dt_c) - step_c(R u_fine(t))) / dt_c.
@@ -139,3 +140,26 @@ def select_alpha(ds: Dataset, mlp, val_runs, candidates=ALPHA_CANDIDATES):
     solver is the reference for the correction: it is one of the candidates)."""
     scores = [(float(np.mean(run_errors(ds, mlp, val_runs, a))), a) for a in candidates]
     return min(scores)[1], scores
+
+
+def prediction_skill(ds: Dataset, mlp, runs):
+    """Per field, the fraction of the one-step defect's variance that the
+    network predicts on the given runs' samples: 1 - sum (f(x) - f(0) - d)^2 /
+    sum (d - mean d)^2 over every snapshot and prognostic node (rbf_mlp_forward
+    per snapshot; the sums are a diagnostic, not part of the corrected run)."""
+    import torch
+    n = ds.coarse_nodes.n_prog
+    se = torch.zeros(4, dtype=torch.float64, device="cuda")
+    s1 = torch.zeros(4, dtype=torch.float64, device="cuda")
+    s2 = torch.zeros(4, dtype=torch.float64, device="cuda")
+    cnt = 0
+    for r in runs:
+        for k in range(ds.n_snap - 1):
+            d = mlp.forward(ds.states[r, k]).double()
+            y = ds.targets[r, k].double()
+            se += ((d - y) ** 2).sum(dim=0)
+            s1 += y.sum(dim=0)
+            s2 += (y ** 2).sum(dim=0)
+            cnt += n
+    var = s2 - s1 ** 2 / cnt
+    return (1.0 - se / torch.clamp(var, min=1e-300)).cpu().numpy()

@@ -33,17 +33,19 @@ class NSParams(C.Structure):
                 ("hv_p", C.c_int32), ("precision", C.c_int32), ("threads_per_node", C.c_int32),
                 ("storage", C.c_int32), ("period_x", C.c_double), ("mu", C.c_double), ("gamma", C.c_double),
                 ("theta_bar", C.c_double), ("g", C.c_double), ("cp", C.c_double), ("cv", C.c_double),
-                ("rd", C.c_double)]
+                ("rd", C.c_double), ("gamma_c", C.c_double), ("spacing", C.c_double)]
 
 
 class AdvParams(C.Structure):
     _fields_ = [("n_sten", C.c_int32), ("phs_p", C.c_int32), ("poly_l", C.c_int32), ("hv_k", C.c_int32),
-                ("hv_p", C.c_int32), ("precision", C.c_int32), ("gamma", C.c_double), ("period_T", C.c_double)]
+                ("hv_p", C.c_int32), ("precision", C.c_int32), ("gamma", C.c_double), ("period_T", C.c_double),
+                ("gamma_c", C.c_double), ("spacing", C.c_double)]
 
 
 class EnsMember(C.Structure):
     _fields_ = [("n_prog", C.c_int64), ("n_all", C.c_int64), ("n_sten", C.c_int32), ("poly_l", C.c_int32),
-                ("period_x", C.c_double), ("gamma", C.c_double), ("dt", C.c_double), ("n_steps", C.c_int64)]
+                ("period_x", C.c_double), ("gamma", C.c_double), ("dt", C.c_double), ("n_steps", C.c_int64),
+                ("spacing", C.c_double)]
 
 
 class Info(C.Structure):
@@ -66,6 +68,7 @@ _lib = None
 _P, _I64, _I32, _D = C.c_void_p, C.c_int64, C.c_int32, C.c_double
 SIGNATURES = [
     ("rbf_last_error", C.c_char_p, []),
+    ("rbf_hyperviscosity_gamma", C.c_int, [_D, _D, _I32, C.POINTER(C.c_double)]),
     ("rbf_build_stencils", C.c_int, [_P, _P, _I64, _I64, _I32, _D, _P, _P]),
     ("rbf_build_stencils_static", C.c_int, [_P, _P, _I64, _I64, _I32, _D, _P, _P]),
     ("rbf_build_weights", C.c_int, [_P, _P, _I64, _P, _I64, _I32, _D, _I32, _I32, _I32, _P, _I32, _P, _P]),
@@ -309,10 +312,11 @@ def lattice_classes(idx, x, z, n_prog, period_x, h, min_members=32):
 
 
 def hyperviscosity_gamma(c, h, k):
-    """gamma = c h^(2k-1): with dt proportional to h this keeps
-    dt * gamma * rho(Delta^k) independent of the resolution (the reading of
-    Sec. 5.3's resolution-independent constant c)."""
-    return c * h ** (2 * k - 1)
+    """The library's gamma of Sec. 5.3 for constant c, spacing h and power k
+    (rbf_hyperviscosity_gamma; host only)."""
+    v = C.c_double()
+    _check(lib().rbf_hyperviscosity_gamma(float(c), float(h), int(k), C.byref(v)))
+    return v.value
 
 
 STORAGE = {"per-node": 0, "lattice": 1}
@@ -323,8 +327,8 @@ def ns_problem(nodes: inp.NodeSet, precision=64, n=37, p=7, l=4, hv_k=3, hv_p=No
     """Navier-Stokes problem on a node set (Sec. 6.2-6.3 defaults)."""
     prm = NSParams(n_sten=n, phs_p=p, poly_l=l, hv_k=hv_k, hv_p=hv_p if hv_p else p, precision=precision,
                    threads_per_node=threads_per_node, storage=STORAGE[storage], period_x=nodes.period_x, mu=mu,
-                   gamma=hyperviscosity_gamma(gamma_c, nodes.h, hv_k) if gamma is None else gamma,
-                   theta_bar=theta_bar, g=inp.G, cp=inp.CP, cv=inp.CV, rd=inp.RD)
+                   gamma=0.0 if gamma is None else gamma, gamma_c=gamma_c if gamma is None else 0.0,
+                   spacing=nodes.h, theta_bar=theta_bar, g=inp.G, cp=inp.CP, cv=inp.CV, rd=inp.RD)
     _torch()
     h = C.c_void_p()
     x = np.ascontiguousarray(nodes.x, np.float64)
@@ -344,7 +348,8 @@ def advection_problem(nodes: inp.NodeSet, precision=64, n=37, p=7, l=4, hv_k=4, 
     flow (one separable part, rbf_adv_create) or the paper's vortex flow (two
     parts, rbf_adv_create_flow)."""
     prm = AdvParams(n_sten=n, phs_p=p, poly_l=l, hv_k=hv_k, hv_p=hv_p, precision=precision,
-                    gamma=hyperviscosity_gamma(gamma_c, nodes.h, hv_k) if gamma is None else gamma, period_T=T)
+                    gamma=0.0 if gamma is None else gamma, gamma_c=gamma_c if gamma is None else 0.0,
+                    spacing=nodes.h, period_T=T)
     _torch()
     x = np.ascontiguousarray(nodes.x, np.float64)
     z = np.ascontiguousarray(nodes.z, np.float64)
@@ -428,12 +433,12 @@ def ensemble_problem(members, precision=32, p=7, hv_k=3, mu=75.0, gamma_c=2.0 **
     common = NSParams(n_sten=37, phs_p=p, poly_l=4, hv_k=hv_k, hv_p=p, precision=precision,
                       threads_per_node=threads_per_node,
                       storage=STORAGE[storage], period_x=0.0, mu=mu, gamma=0.0, theta_bar=theta_bar, g=inp.G, cp=inp.CP,
-                      cv=inp.CV, rd=inp.RD)
+                      cv=inp.CV, rd=inp.RD, gamma_c=gamma_c)
     arr = (EnsMember * len(members))()
     for r, m in enumerate(members):
         arr[r] = EnsMember(n_prog=m.nodes.n_prog, n_all=m.nodes.n_all, n_sten=m.n, poly_l=m.l,
-                           period_x=m.nodes.period_x, gamma=hyperviscosity_gamma(gamma_c, m.nodes.h, hv_k),
-                           dt=m.dt, n_steps=m.n_steps)
+                           period_x=m.nodes.period_x, gamma=0.0, dt=m.dt, n_steps=m.n_steps,
+                           spacing=m.nodes.h)
     x = np.ascontiguousarray(np.concatenate([m.nodes.x for m in members]), np.float64)
     z = np.ascontiguousarray(np.concatenate([m.nodes.z for m in members]), np.float64)
     kind = np.ascontiguousarray(np.concatenate([m.nodes.kind for m in members]), np.int32)

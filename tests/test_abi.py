@@ -61,9 +61,42 @@ def test_argument_errors_need_no_gpu(lib):
     assert b"threads per node" in lib.rbf_last_error()
 
 
-def test_struct_layouts_match_header():
+def _c_layouts(tmp_path, structs):
+    """sizeof and every field's offsetof of the header's structs, printed by a
+    C program compiled against include/rbffd.h (gcc)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rbffd.h"', "int main(void) {"]
+    for cname, fields in structs.items():
+        lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f in fields:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    return {(a, b): int(v) for a, b, v in (ln.split() for ln in out.strip().splitlines())}
+
+
+def test_struct_layouts_match_header(tmp_path):
     from paper_1509_02615_gb300 import rbffd
-    # 8 int32 + 8 doubles; 6 int32 + 2 doubles; see include/rbffd.h
-    assert C.sizeof(rbffd.NSParams) == 8 * 4 + 8 * 8
-    assert C.sizeof(rbffd.AdvParams) == 6 * 4 + 2 * 8
-    assert C.sizeof(rbffd.Info) == 3 * 8 + 10 * 4 + 4 * 8 + 6 * 4
+    pairs = {"rbf_ns_params": rbffd.NSParams, "rbf_adv_params": rbffd.AdvParams,
+             "rbf_ens_member": rbffd.EnsMember, "rbf_info": rbffd.Info}
+    got = _c_layouts(tmp_path, {c: [f for f, _ in py._fields_] for c, py in pairs.items()})
+    for cname, py in pairs.items():
+        assert got[(cname, "sizeof")] == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_hyperviscosity_gamma_needs_no_gpu(lib):
+    from paper_1509_02615_gb300 import rbffd
+    assert rbffd.hyperviscosity_gamma(2.0 ** -6, 100.0, 3) == pytest.approx(2.0 ** -6 * 100.0 ** 5, rel=1e-15)
+    v = C.c_double()
+    assert lib.rbf_hyperviscosity_gamma(1.0, 0.0, 3, C.byref(v)) == rbffd.RBF_E_ARG
+    assert lib.rbf_hyperviscosity_gamma(-1.0, 1.0, 3, C.byref(v)) == rbffd.RBF_E_ARG

@@ -118,21 +118,25 @@ def test_forward_matches_oracle(small_data):
 
 
 def test_correction_on_held_out_seeds():
-    """800 m coarse runs corrected by an MLP trained on 200 m FP64 runs
-    restricted to the coarse nodes (10 training seeds); the per-field strength
-    is chosen on 3 validation seeds, with the uncorrected solver as a
-    candidate; 3 held-out seeds are scored at 900 s against the restricted
-    200 m reference.  The corrected error must not exceed the uncorrected one
-    (2% slack for the validation-to-test spread)."""
+    """400 m coarse runs corrected by an MLP trained on 100 m FP64 runs
+    restricted to the coarse nodes (10 training seeds, 30k iterations: the
+    bench's setting); the per-field strength is chosen on 3 validation seeds
+    among candidates that include the uncorrected solver; 3 held-out seeds are
+    scored at 900 s against the restricted 100 m reference.  The selected
+    strength must be non-zero and the corrected mean error at least 15% below
+    the uncorrected one (the bench measures about 30%)."""
     seeds = inp.learned_correction_seeds(16, seed=1)
-    ds = learned.build_dataset(800.0, 4, seeds, 900.0)
-    mlp, loss = learned.train(ds, 10, iters=3000, batch=4096, lr=2e-3)
+    ds = learned.build_dataset(400.0, 4, seeds, 900.0)
+    mlp, loss = learned.train(ds, 10, iters=30000, batch=4096, lr=2e-3)
     assert loss[-50:].mean() < 0.2 * loss[:50].mean()
     alpha, scores = learned.select_alpha(ds, mlp, range(10, 13))
     test = range(13, 16)
     ep = learned.run_errors(ds, mlp, test, (0.0, 0.0, 0.0, 0.0))
     el = learned.run_errors(ds, mlp, test, alpha)
+    skill = learned.prediction_skill(ds, mlp, range(10, 13))
     print("validation scores", scores)
-    print("selected alpha", alpha, "held-out relative l2 [u, w, theta', pi']: uncorrected", ep, "corrected", el)
+    print("selected alpha", alpha, "held-out relative l2 [u, w, theta', pi']: uncorrected", ep, "corrected", el,
+          f"gain {1.0 - np.mean(el) / np.mean(ep):.3f}; validation skill per field", skill)
     assert np.all(np.isfinite(el))
-    assert np.mean(el) <= 1.02 * np.mean(ep)
+    assert any(a > 0.0 for a in alpha), alpha
+    assert np.mean(el) < 0.85 * np.mean(ep), (np.mean(el), np.mean(ep))

@@ -3,13 +3,10 @@
 Tolerances (relative l2 unless stated):
   * stencils: identical index lists (bit-exact: both sides order by the same
     FP64 squared distance, then index);
-  * FP64 weights: 0.05 * kappa_max * eps64, kappa_max the largest 2-norm
-    condition number of the scaled augmented systems (measured in the test):
-    two different backward-stable partial-pivoting LU codes agree to
-    O(kappa * eps); in l2 over all weights the gap is far below the bound;
-  * FP64 right-hand side: 1e-11 per field (weights as above, plain sums in
-    both codes);
-  * FP64 RK4 steps: 1e-10 per field after 10 steps;
+  * FP64 weights, right-hand sides, ghost values and RK4 steps: per output
+    max(1e-12, 10 s), s the oracle's own spread between stencil orders
+    (tests/fp64_bounds.py); the largest 2-norm condition number of the
+    scaled augmented systems is printed beside the weights;
   * FP32: per-field bounds stated in each test (FP32 weights and arithmetic,
     eps32 = 6e-8, difference form).
 """
@@ -24,8 +21,11 @@ from oracle import stencils as ost  # noqa: E402
 from oracle import weights as owt  # noqa: E402
 from oracle.advection import AdvectionOracle  # noqa: E402
 from oracle.ns import NSOracle, front_location  # noqa: E402
+from oracle.operators import stencil_permutation  # noqa: E402
 from paper_1509_02615_gb300 import inputs as inp  # noqa: E402
 from paper_1509_02615_gb300 import rbffd  # noqa: E402
+
+import fp64_bounds as fb  # noqa: E402
 
 
 def rel(a, b):
@@ -76,14 +76,20 @@ def test_weights_fp64(p, l, k):
     ops = ["dx", "dz", "lap", "dxx", "dzz"]
     w = rbffd.build_weights(_t(nodes.x), _t(nodes.z), _t(idx, torch.int32), p, l, ops, 0, nodes.period_x).cpu().numpy()
     hv = rbffd.build_weights(_t(nodes.x), _t(nodes.z), _t(idx, torch.int32), p, l, ["hv"], k, nodes.period_x).cpu().numpy()
-    ref = owt.all_weights(nodes.x, nodes.z, idx, p, l, ops, 0, nodes.period_x)
-    href = owt.all_weights(nodes.x, nodes.z, idx, p, l, ["hv"], k, nodes.period_x)
+
+    def oracle_weights(order):
+        # weights of the same stencils listed in another order, put back in
+        # the ranked order
+        perm = stencil_permutation(order, n)
+        a = owt.all_weights(nodes.x, nodes.z, idx[:, perm], p, l, ops, 0, nodes.period_x)
+        b = owt.all_weights(nodes.x, nodes.z, idx[:, perm], p, l, ["hv"], k, nodes.period_x)
+        return np.concatenate([a, b])[:, :, np.argsort(perm)]
+
+    ref, s = fb.with_spread(lambda order: order, oracle_weights)
     kappa = max(owt.condition_number(nodes.x, nodes.z, idx[i], p, l, nodes.period_x)
                 for i in range(0, nodes.n_prog, 37))
-    tol = max(1e-12, 0.05 * kappa * np.finfo(np.float64).eps)
-    errs = [rel(w[o], ref[o]) for o in range(len(ops))] + [rel(hv[0], href[0])]
-    print(f"p={p} l={l} kappa_max={kappa:.3e} tol={tol:.2e} rel_l2={['%.2e' % e for e in errs]}")
-    assert max(errs) < tol, errs
+    print(f"p={p} l={l} kappa_max={kappa:.3e} (0.05 kappa eps = {0.05 * kappa * np.finfo(np.float64).eps:.1e})")
+    fb.check(np.concatenate([w, hv]), ref, s, f"weights p={p} l={l}")
 
 
 def test_weights_singular_stencil_is_reported():
@@ -109,46 +115,55 @@ def dc800():
     return nodes, o, U
 
 
-def test_ns_rhs_fp64(dc800):
+@pytest.fixture(scope="module")
+def dc800_fp64_ref(dc800):
+    """The oracle's right-hand side and ghost values at the 60-step state,
+    with their spreads over stencil orders."""
     nodes, o, U = dc800
+
+    def outputs(orc):
+        V = U.copy()
+        orc.fill_ghosts(V)
+        return orc.rhs(0.0, U), V[:, nodes.n_prog:]
+
+    res = {order: outputs(o if order == "nearest" else NSOracle(nodes, stencil_order=order))
+           for order in ("nearest",) + fb.ORDERS}
+    rhs, s_rhs = fb.with_spread(lambda order: order, lambda order: res[order][0])
+    gh, s_gh = fb.with_spread(lambda order: order, lambda order: res[order][1])
+    return rhs, s_rhs, gh, s_gh
+
+
+def test_ns_rhs_fp64(dc800, dc800_fp64_ref):
+    nodes, o, U = dc800
+    ref, s, gref, gs = dc800_fp64_ref
     pb = rbffd.ns_problem(nodes, precision=64, threads_per_node=4)
     Ud = rbffd.state_tensor(U, 64)
     got = rbffd.fields(pb.rhs(0.0, Ud))
-    ref = o.rhs(0.0, U)
-    print("fp64 rhs rel l2 per field", [f"{rel(got[f], ref[f]):.2e}" for f in range(4)])
-    for f in range(4):
-        assert rel(got[f], ref[f]) < 1e-11, (f, rel(got[f], ref[f]))
+    fb.check(got, ref, s, "density current 800 m RHS")
     # the ghost entries written into U solve the ghost systems
-    V = U.copy()
-    o.fill_ghosts(V)
-    gh = rbffd.fields(Ud)[:, nodes.n_prog:]
-    for f in range(4):
-        assert rel(gh[f], V[f, nodes.n_prog:]) < 1e-11
+    fb.check(rbffd.fields(Ud)[:, nodes.n_prog:], gref, gs, "density current 800 m ghost values")
 
 
 @pytest.mark.parametrize("G", [1, 2, 4, 8])
-def test_ns_rhs_fp64_every_lane_split(dc800, G):
+def test_ns_rhs_fp64_every_lane_split(dc800, dc800_fp64_ref, G):
     nodes, o, U = dc800
+    ref, s, _, _ = dc800_fp64_ref
     pb = rbffd.ns_problem(nodes, precision=64, threads_per_node=G)
     got = rbffd.fields(pb.rhs(0.0, rbffd.state_tensor(U, 64)))
-    ref = o.rhs(0.0, U)
-    for f in range(4):
-        assert rel(got[f], ref[f]) < 1e-11
+    fb.check(got, ref, s, f"RHS G={G}")
 
 
 def test_ns_rk4_fp64_steps():
     nodes = inp.density_current_nodes(400.0)
-    o = NSOracle(nodes)
     U0 = inp.density_current_state(nodes)
-    ref = o.run(U0, 0.0, 1.0, 10)
+    P = nodes.n_prog
+    ref, s = fb.with_spread(lambda order: NSOracle(nodes, stencil_order=order),
+                            lambda o: o.run(U0, 0.0, 1.0, 10)[:, :P])
     pb = rbffd.ns_problem(nodes, precision=64)
     Ud = rbffd.state_tensor(U0, 64)
-    for s in range(10):
-        pb.rk4_step(s * 1.0, 1.0, Ud)
-    got = rbffd.fields(Ud)
-    print("fp64 10-step rel l2 per field", [f"{rel(got[f, :nodes.n_prog], ref[f, :nodes.n_prog]):.2e}" for f in range(4)])
-    for f in range(4):
-        assert rel(got[f, :nodes.n_prog], ref[f, :nodes.n_prog]) < 1e-10
+    for step in range(10):
+        pb.rk4_step(step * 1.0, 1.0, Ud)
+    fb.check(rbffd.fields(Ud)[:, :P], ref, s, "density current 400 m, 10 steps")
 
 
 def test_run_graph_equals_steps_bitwise():
@@ -218,16 +233,16 @@ def test_minmax_and_nonfinite(dc800):
 
 def test_advection_fp64():
     nodes = inp.unit_square_mirrored(32)
-    o = AdvectionOracle(nodes)
     psi0 = inp.cosine_bell(nodes.x[:nodes.n_prog], nodes.z[:nodes.n_prog])
+    orc = {order: AdvectionOracle(nodes, stencil_order=order) for order in ("nearest",) + fb.ORDERS}
     pb = rbffd.advection_problem(nodes, precision=64)
     P = rbffd.state_tensor(psi0, 64)
-    got = rbffd.fields(pb.rhs(0.7, P))[0]
-    ref = o.rhs(0.7, psi0)[0]
-    assert rel(got, ref) < 1e-11
+    got = rbffd.fields(pb.rhs(0.7, P))
+    ref, s = fb.with_spread(lambda order: orc[order], lambda o: o.rhs(0.7, psi0))
+    fb.check(got, ref, s, "advection 32^2 RHS")
     pb.run(0.0, 0.005, 50, P)
-    ref = o.run(psi0, 0.0, 0.005, 50)[0]
-    assert rel(rbffd.fields(P)[0], ref) < 1e-10
+    ref, s = fb.with_spread(lambda order: orc[order], lambda o: o.run(psi0, 0.0, 0.005, 50))
+    fb.check(rbffd.fields(P), ref, s, "advection 32^2, 50 steps")
 
 
 def test_density_current_100m_matches_paper_table():

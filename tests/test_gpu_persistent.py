@@ -4,12 +4,16 @@ banded inverse rows, one grid barrier per stage.  Checked against the FP64
 oracle, against the graph mode, and on its bounded-wait failure path.
 
 Tolerances (relative l2 per field over the prognostic nodes):
-  * FP64 against the oracle: 1e-12 after the stated steps;
+  * FP64 against the oracle: per field below max(1e-12, 10 s), s the oracle's
+    own spread between stencil orders (tests/fp64_bounds.py); 1e-12 flat on
+    the density current at 400 m, whose spread is far below it;
   * FP64 against the graph mode: 1e-13 (the two differ only in the order of
     the ghost sums and in inverse entries below 2^-8 eps of their row);
   * FP32 against the graph mode: 1e-5 after the stated steps (the same
     differences at eps32 = 6e-8, grown over the run).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -20,6 +24,8 @@ pytestmark = pytest.mark.gpu
 from oracle.ns import NSOracle  # noqa: E402
 from paper_1509_02615_gb300 import inputs as inp  # noqa: E402
 from paper_1509_02615_gb300 import rbffd  # noqa: E402
+
+import fp64_bounds as fb  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -103,18 +109,15 @@ def test_persistent_walled_bubble_fp64_matches_oracle():
     classes."""
     from paper_1509_02615_gb300 import configs
     wl = configs.bubble(h=500.0, seed=1, t_end=30.0)
-    o = NSOracle(wl.nodes, **wl.params)
-    ref = o.run(wl.U0, 0.0, wl.dt, wl.n_steps)
+    P = wl.nodes.n_prog
+    ref, s = fb.with_spread(lambda order: NSOracle(wl.nodes, stencil_order=order, **wl.params),
+                            lambda o: o.run(wl.U0, 0.0, wl.dt, wl.n_steps)[:, :P])
     pb = rbffd.ns_problem(wl.nodes, precision=64, threads_per_node=2, **wl.params)
     pb.set_run_mode("persistent", lanes=2)
     U = rbffd.state_tensor(wl.U0, 64)
     pb.run(0.0, wl.dt, wl.n_steps, U)
     pb.sync()
-    got = rbffd.fields(U)
-    P = wl.nodes.n_prog
-    errs = [rel(got[f, :P], ref[f, :P]) for f in (1, 2, 3)]   # u stays at rounding level
-    print("persistent FP64 bubble vs oracle:", [f"{e:.2e}" for e in errs])
-    assert max(errs) < 1e-10
+    fb.check(rbffd.fields(U)[:, :P], ref, s, "persistent FP64 bubble 500 m")
 
 
 def test_persistent_timeout_reports_and_recovers():
@@ -186,25 +189,31 @@ def test_bench_launch_configuration_matches_oracle_at_full_size(prec):
     the launch configuration the bench times (persistent, one lane per node,
     one CTA per SM), two RK4 steps from the density-current state, against
     two oracle steps.  FP64: relative l2 per field of the change over the two
-    steps (the state itself is dominated by the initial theta') below 1e-9.
-    FP32: relative l2 per field of the state below 1e-5 (u, w and pi' start
-    at zero, so for them this is the change; theta' changes by ~1e-4 of
-    itself, below its FP32 representation)."""
+    steps (the state itself is dominated by the initial theta') below
+    max(1e-12, 10 s), s the oracle's own spread between stencil orders for
+    that change.  FP32: relative l2 per field of the state below 1e-5 (u, w
+    and pi' start at zero, so for them this is the change; theta' changes by
+    ~1e-4 of itself, below its FP32 representation)."""
     nodes = inp.density_current_nodes(100.0)
     U0 = inp.density_current_state(nodes)
-    ref = NSOracle(nodes).run(U0, 0.0, 0.25, 2)
+    P = nodes.n_prog
+    workers = min(16, os.cpu_count() or 1)
+    if prec == 64:
+        dref, s = fb.with_spread(lambda order: NSOracle(nodes, stencil_order=order, workers=workers),
+                                 lambda o: o.run(U0, 0.0, 0.25, 2)[:, :P] - U0[:, :P])
+    else:
+        ref = NSOracle(nodes, workers=workers).run(U0, 0.0, 0.25, 2)
     pb = rbffd.ns_problem(nodes, precision=prec, threads_per_node=1)
     pb.set_run_mode("persistent", lanes=1, ctas=152 if prec == 32 else 0)
     assert pb.info()["run_mode"] == 2
     U = rbffd.state_tensor(U0, prec)
     pb.run(0.0, 0.25, 2, U)
     pb.sync()
-    P = nodes.n_prog
     got = rbffd.fields(U)[:, :P]
     if prec == 64:
-        errs = [rel(got[f] - U0[f, :P], ref[f, :P] - U0[f, :P]) for f in range(4)]
+        fb.check(got - U0[:, :P], dref, s, "persistent, 100 m, change over 2 steps")
     else:
         errs = [rel(got[f], ref[f, :P]) for f in range(4)]
-    print(f"FP{prec} persistent, 100 m, 2 steps vs oracle", ["%.1e" % e for e in errs])
-    assert max(errs) < (1e-9 if prec == 64 else 1e-5), errs
+        print(f"FP{prec} persistent, 100 m, 2 steps vs oracle", ["%.1e" % e for e in errs])
+        assert max(errs) < 1e-5, errs
     pb.close()

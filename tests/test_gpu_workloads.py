@@ -2,12 +2,13 @@
 warm-bubble workloads (walled box, scattered nodes, n = 56, r^9 + deg 5:
 lateral-wall and corner ghost systems).
 
-Tolerances: FP64 GPU vs FP64 oracle 1e-10 relative l2 after the stated steps
-(the per-step parity of 1e-11 with RK4's mild growth); the bubble's FP64
-right-hand side within 0.05 kappa_max eps64 of the term scale (the weight
-parity bound); FP32 vs FP64 per-field bounds stated in each test (eps32 ~
-6e-8 amplified by the run).
+Tolerances: FP64 GPU vs FP64 oracle per field below max(1e-12, 10 s), s the
+oracle's own spread between stencil orders for the same outputs
+(tests/fp64_bounds.py); FP32 vs FP64 per-field bounds stated in each test
+(eps32 ~ 6e-8 amplified by the run).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -22,6 +23,8 @@ from oracle.ns import NSOracle  # noqa: E402
 from paper_1509_02615_gb300 import configs  # noqa: E402
 from paper_1509_02615_gb300 import inputs as inp  # noqa: E402
 from paper_1509_02615_gb300 import rbffd  # noqa: E402
+
+import fp64_bounds as fb  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -38,81 +41,74 @@ def rel(a, b):
 
 def test_advection_full_period_fp64_and_fp32():
     wl = configs.advection(64)
-    o = AdvectionOracle(wl.nodes, **wl.params)
-    ref = o.run(wl.U0, 0.0, wl.dt, wl.n_steps)[0]
+    ref, s = fb.with_spread(lambda order: AdvectionOracle(wl.nodes, stencil_order=order, **wl.params),
+                            lambda o: o.run(wl.U0, 0.0, wl.dt, wl.n_steps))
     pb = rbffd.advection_problem(wl.nodes, precision=64, **wl.params)
     P = rbffd.state_tensor(wl.U0, 64)
     pb.run(0.0, wl.dt, wl.n_steps, P)
-    got = rbffd.fields(P)[0]
-    e = rel(got, ref)
-    ret_gpu, ret_ref = rel(got, wl.U0), rel(ref, wl.U0)
-    print(f"advection 64^2, t = T: GPU vs oracle {e:.2e}; return error GPU {ret_gpu:.6f} oracle {ret_ref:.6f}")
-    assert e < 1e-10
+    got = rbffd.fields(P)
+    fb.check(got, ref, s, "advection 64^2, t = T")
+    print(f"return error GPU {rel(got[0], wl.U0):.6f} oracle {rel(ref[0], wl.U0):.6f}")
     pb32 = rbffd.advection_problem(wl.nodes, precision=32, **wl.params)
     Q = rbffd.state_tensor(wl.U0, 32)
     pb32.run(0.0, wl.dt, wl.n_steps, Q)
-    e32 = rel(rbffd.fields(Q)[0], ref)
+    e32 = rel(rbffd.fields(Q)[0], ref[0])
     print(f"advection FP32 vs FP64 oracle at t = T: {e32:.2e}")
     assert e32 < 1e-4
 
 
-def term_scale(o, U):
-    """Per field, per node: the sum of the magnitudes of the terms of
-    Eqs. (uEq)-(piEq) (each stencil sum taken with |w_ij| |f_j|).  Two FP64
-    evaluations that differ only by rounding in the weights and the sums
-    differ by about eps * kappa * this scale; where the terms cancel (a
-    smooth field's dissipation), it is far above |tendency|."""
-    V = np.array(U, dtype=np.float64, copy=True)
-    o.fill_ghosts(V)
-    A = {k: abs(M) for k, M in o.D.items()}
-    P = o.n_prog
-    au, aw, at, ap = np.abs(V)
-    up, wp, tp, pp = np.abs(V[:, :P])
-    cpth = np.abs(inp.CP * (o.theta_bar + V[2, :P]))
-    diss = lambda f: o.mu * (A["lap"] @ f) + abs(o.hv_coef) * (A["hv"] @ f)
-    su = up * (A["dx"] @ au) + wp * (A["dz"] @ au) + cpth * (A["dx"] @ ap) + diss(au)
-    sw = up * (A["dx"] @ aw) + wp * (A["dz"] @ aw) + cpth * (A["dz"] @ ap) + inp.G * tp / o.theta_bar + diss(aw)
-    st = up * (A["dx"] @ at) + wp * (A["dz"] @ at) + diss(at)
-    sp = (up * (A["dx"] @ ap) + wp * (abs(o.dpibar) + A["dz"] @ ap)
-          + (inp.RD / inp.CV) * np.abs(o.pibar + V[3, :P]) * ((A["dx"] @ au) + (A["dz"] @ aw))
-          + abs(o.hv_coef) * (A["hv"] @ ap))
-    return np.stack([su, sw, st, sp])
-
-
 def test_bubble_small_fp64_matches_oracle():
-    """RHS parity in FP64 measured against the term scale (the bubble's r^9 +
-    deg-5, n = 56 weights are less well conditioned than the density
-    current's, and its theta' tendency at rest is a strongly cancelling
-    dissipation sum), then 48 RK4 steps against the oracle."""
+    """The bubble workload's method (r^9 + deg 5, n = 56, walls on all sides,
+    corner ghosts) at 500 m: the FP64 right-hand side at the initial state
+    and 48 RK4 steps against the oracle.  At rest u's tendency is rounding
+    noise around zero on both sides, and theta''s is a strongly cancelling
+    dissipation sum; the oracle's spread over stencil orders is large for
+    both (kappa_max ~7e8), and the bound follows it."""
     wl = configs.bubble(h=500.0, seed=1, t_end=60.0)
-    o = NSOracle(wl.nodes, **wl.params)
-    ref = o.run(wl.U0, 0.0, wl.dt, wl.n_steps)
+    orc = {order: NSOracle(wl.nodes, stencil_order=order, **wl.params) for order in ("nearest",) + fb.ORDERS}
     pb = rbffd.ns_problem(wl.nodes, precision=64, **wl.params)
     U = rbffd.state_tensor(wl.U0, 64)
     r0 = rbffd.fields(pb.rhs(0.0, U.clone()))
-    rref = o.rhs(0.0, wl.U0)
-    scale = term_scale(o, wl.U0)
-    # the weight parity bound: two partial-pivoting LU codes give weights
-    # that agree to O(kappa eps), kappa the augmented systems' condition
+    rref, rs = fb.with_spread(lambda order: orc[order], lambda o: o.rhs(0.0, wl.U0))
     nd = wl.nodes
     idx = ost.knn(nd.x, nd.z, np.arange(nd.n_prog), 56, nd.period_x)
     kappa = max(owt.condition_number(nd.x, nd.z, idx[i], 9, 5, nd.period_x) for i in range(0, nd.n_prog, 8))
-    tol = max(1e-12, 0.05 * kappa * np.finfo(np.float64).eps)
-    print(f"kappa_max {kappa:.2e}, bound {tol:.2e}")
-    for f in range(4):
-        if np.abs(rref[f]).max() < 1e-20:
-            # a field at rest: both sides give rounding noise around zero
-            assert np.abs(r0[f]).max() < 1e-20
-        else:
-            e = np.linalg.norm(r0[f] - rref[f]) / np.linalg.norm(scale[f])
-            print(f"field {f}: |d| / |terms| = {e:.2e}, |d| / |rhs| = {rel(r0[f], rref[f]):.2e}")
-            assert e < tol, (f, e)
+    print(f"kappa_max {kappa:.2e}")
+    # at rest, u and pi' have tendencies below 1e-20 on both sides (the bubble's
+    # tail at the walls is ~1e-32 K): rounding noise around zero, checked as such
+    rest = [f for f in range(4) if np.abs(rref[f]).max() < 1e-20]
+    live = [f for f in range(4) if f not in rest]
+    for f in rest:
+        assert np.abs(r0[f]).max() < 1e-20, f
+    fb.check(r0[live], rref[live], rs[live], f"bubble 500 m RHS at rest, fields {live}")
+    P = nd.n_prog
+    ref, s = fb.with_spread(lambda order: orc[order], lambda o: o.run(wl.U0, 0.0, wl.dt, wl.n_steps)[:, :P])
     pb.run(0.0, wl.dt, wl.n_steps, U)
-    got = rbffd.fields(U)
-    P = wl.nodes.n_prog
-    errs = [rel(got[f, :P], ref[f, :P]) for f in range(4)]
-    print("bubble 500 m, 48 steps: GPU vs oracle", errs)
-    assert max(errs) < 1e-10
+    fb.check(rbffd.fields(U)[:, :P], ref, s, "bubble 500 m, 48 steps")
+
+
+def test_bubble_full_size_fp64_matches_oracle():
+    """The bubble workload at full size -- 308,097 scattered nodes at 25 m,
+    n = 56, r^9 + deg 5 -- in the launch configuration the bench times
+    (FP64, lanes and run mode autotuned at creation): two RK4 steps from the
+    initial state against two oracle steps.  Per field, the relative l2 of
+    the change over the two steps (theta' itself is dominated by the initial
+    bubble) below max(1e-12, 10 s), s the oracle's own spread for that
+    change.  The oracle solves its weights in worker processes."""
+    wl = configs.bubble(h=25.0, seed=1, t_end=1000.0)
+    nd = wl.nodes
+    P = nd.n_prog
+    workers = min(16, os.cpu_count() or 1)
+    dref, s = fb.with_spread(lambda order: NSOracle(nd, stencil_order=order, workers=workers, **wl.params),
+                             lambda o: o.run(wl.U0, 0.0, wl.dt, 2)[:, :P] - wl.U0[:, :P])
+    pb = rbffd.ns_problem(nd, precision=64, **wl.params)
+    info = pb.info()
+    U = rbffd.state_tensor(wl.U0, 64)
+    pb.run(0.0, wl.dt, 2, U)
+    pb.sync()
+    print(f"bubble 25 m FP64: {P} nodes, run mode {info['run_mode']}, {info['threads_per_node']} lanes per node")
+    fb.check(rbffd.fields(U)[:, :P] - wl.U0[:, :P], dref, s, "bubble 25 m, change over 2 steps")
+    pb.close()
 
 
 def test_bubble_full_size_fp32_vs_fp64():
