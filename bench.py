@@ -397,7 +397,7 @@ def density_current_case(torch, args, pk, pk_kind, p64, flush):
     dt = args.h / 400.0
     U = rbffd.state_tensor(U0, 32)
     persistent = info["run_mode"] == 2
-    step_ms, _ = time_steps(torch, pb, U, dt, args.steps, args.warmup, flush, False)
+    step_ms, _ = time_steps(torch, pb, U, dt, args.steps, args.warmup, flush, False, nvtx="dc_timed")
     stage_ms = [] if persistent else time_steps(torch, pb, U, dt, args.steps, 1, flush, True)[1]
     if persistent:
         avg_ms, bpl, kernel, share = float(np.mean(step_ms)), 4.0 * info["rhs_bytes_per_node"] * nodes.n_prog, \
@@ -502,10 +502,12 @@ def weights_case(torch, nodes, n, p, l, hv_k, peak_tflops, label):
     build()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push(f"weights_S{n + (l + 1) * (l + 2) // 2}")
     e0.record(stream)
     build()
     e1.record(stream)
     e1.synchronize()
+    torch.cuda.nvtx.range_pop()
     ms = e0.elapsed_time(e1)
     S = n + (l + 1) * (l + 2) // 2
     flops = nodes.n_prog * ((2.0 / 3.0) * S ** 3 + 2.0 * len(ops) * S ** 2)

@@ -288,7 +288,14 @@ void build_weights(const double *x, const double *z, int64_t n_all, const int32_
     RBF_REQUIRE(x && z && idx && w, "null pointer argument");
     job.ld = (job.S + n_ops) | 1;   // odd leading dimension: fewer bank conflicts
     size_t per_warp = ((size_t)job.S * job.ld + 2 * n + 8) * sizeof(double);
-    int warps = (int)std::min<size_t>(8, (200 * 1024) / per_warp);
+    // as many systems per CTA (one CTA per SM) as the 227 KB of shared memory
+    // a CTA may hold, up to 8: the SM's four sub-partitions each have their
+    // own share of the FP64 pipe, so fewer than four warps leave part of it
+    // idle (S = 77: 52 KB per system, 4 warps)
+    int max_smem = 0, dev = 0;
+    RBF_CUDA(cudaGetDevice(&dev));
+    RBF_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    int warps = (int)std::min<size_t>(8, (size_t)max_smem / per_warp);
     RBF_REQUIRE(warps >= 1, "weight system too large for shared memory");
     RBF_CUDA(cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(warps * per_warp)));
     DevBuf<int> bad(1);
