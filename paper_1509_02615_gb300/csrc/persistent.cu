@@ -114,6 +114,12 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// waits until at most N of this thread's committed copy groups are pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait_pending() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 // record j of U into record slot k of the shared list (one or two 16-byte copies)
 __device__ __forceinline__ void cp_rec(float *S, int k, const float *U, int64_t j) {
     cp_async16(S + (size_t)k * 4, U + j * 4);
@@ -171,13 +177,46 @@ __device__ bool grid_barrier(unsigned *arrive, int *abort, unsigned &target, lon
     return s_ok != 0;
 }
 
+// Barrier among `members` CTAs only (the others never call it), with the same
+// bounded wait and abort protocol as grid_barrier.
+__device__ bool group_barrier(unsigned *arrive, int *abort, unsigned &target, unsigned members, long long limit) {
+    __shared__ int s_ok2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        target += members;
+        __threadfence();
+        red_release_add(arrive, 1u);
+        int ok = 1;
+        long long polls = 0;
+        while ((int)(ld_acquire(arrive) - target) < 0) {
+            if (ld_relaxed(abort)) { ok = 0; break; }
+            if (++polls > limit) {
+                st_relaxed(abort, 1);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        if (ok && ld_relaxed(abort)) ok = 0;
+        __threadfence();
+        s_ok2 = ok;
+    }
+    __syncthreads();
+    return s_ok2 != 0;
+}
+
 // Layout of one CTA's block (host-built, identical on both sides).
 struct CtaInfo {
     int32_t list_off;   // first entry of its record list in hlist
     int32_t n_own;      // own nodes (open the list)
     int32_t n_load;     // records copied from the stage input every stage
+    int32_t n_wload;    // of those after the own nodes, the first n_wload are the
+                        // records its wall rows read (copied as their own group)
     int32_t n_list;     // plus the ghosts it solves (close the list)
-    int32_t n_rows;     // wall rows whose residuals it forms
+    int32_t n_rows;     // wall rows whose residuals its ghost solve reads (the band)
+    int32_t n_crows;    // wall rows whose residuals it forms: the band rows, or in
+                        // owned-rows mode the rows of its own wall nodes
+    int32_t o_ogp, o_brow;   // owned-rows mode: global row of each formed row, of each band row
     int32_t n_gc;       // (ghost, operator class) pairs it solves
     int32_t n_set;      // weight sets per wall row
     int32_t n_coef;     // band coefficients of all its pairs
@@ -210,6 +249,12 @@ struct PArgs {
     unsigned base;                  // its value when this launch starts
     int *abort;
     long long spin_limit;
+    // owned-rows mode
+    int own_rows, wall_ctas;
+    int64_t ng;                     // ghost rows (stride of resg)
+    T *resg;                        // [4][ng]
+    unsigned *arrive2;
+    unsigned base2;
     // a9 (MLP variants): network, scales, strengths
     const __nv_bfloat16 *mW;        // BF16 parameters (W1 at oW1, W2 at oW2, W3 at oW3)
     const float *mP;                // FP32 parameters (biases)
@@ -534,8 +579,10 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
         const Rec<T> r0 = ld_rec_cg(a.U, i);
         un[0] = r0.u; un[1] = r0.w; un[2] = r0.t; un[3] = r0.p;
     }
-    unsigned target = a.base;
+    unsigned target = a.base, target2 = a.base2;
     T o4[4] = {0, 0, 0, 0};   // the node's latest stage output
+    const int32_t *ogp = reinterpret_cast<const int32_t *>(blob + ci.o_ogp);
+    const int32_t *brow = reinterpret_cast<const int32_t *>(blob + ci.o_brow);
 
     for (int64_t step = 0; step < a.n_steps; ++step) {
         for (int st = 0; st < 4; ++st) {
@@ -543,24 +590,35 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
             T *Uout = st == 0 ? a.S0 : st == 1 ? a.S1 : st == 2 ? a.S0 : a.U;
             // ---- the CTA's records of the stage input: its own nodes' from
             // registers (it wrote them), the others through L2 ----------------
+            // The records the wall rows read go first, as their own copy
+            // group: the residuals and the ghost solve start once they have
+            // landed, while the rest of the list is still in flight.
             const bool first = step == 0 && st == 0;
             if (!first && live && g == 0) sh_store(halo, li, Rec<T>{o4[0], o4[1], o4[2], o4[3]});
-            for (int k = (first ? ci.n_load : ci.n_own) + threadIdx.x; k < ci.n_load; k += blockDim.x)
-                cp_rec(halo, k, Uin, __ldg(hl + k));
-            cp_async_wait();   // (at the first stage: the constant block and the records issued at entry)
+            if (first) {
+                cp_async_wait();   // the constant block and the records issued at entry
+            } else {
+                const int wend = ci.n_own + ci.n_wload;
+                for (int k = ci.n_own + threadIdx.x; k < wend; k += blockDim.x) cp_rec(halo, k, Uin, __ldg(hl + k));
+                cp_async_commit();
+                for (int k = wend + threadIdx.x; k < ci.n_load; k += blockDim.x) cp_rec(halo, k, Uin, __ldg(hl + k));
+                cp_async_commit();
+                if (ci.n_rows > 0 || ci.n_crows > 0) cp_async_wait_pending<1>();
+                else cp_async_wait_pending<0>();
+            }
             __syncthreads();
-            if (ci.n_rows > 0) {
+            if (ci.n_crows > 0) {
                 // ---- residuals b - W_I u_I - W_B u_B of its wall rows -----------
                 // L lanes per row, L the largest of 8, 4, 2, 1 that lets one pass
                 // of the CTA's threads cover every row
-                const int L = lanes_for(ci.n_rows, blockDim.x, kRowLanes);
+                const int L = lanes_for(ci.n_crows, blockDim.x, kRowLanes);
                 const int per = a.npad / L;
-                const int nlr = (ci.n_rows * L + 31) & ~31;
+                const int nlr = (ci.n_crows * L + 31) & ~31;
                 for (int e = threadIdx.x; e < nlr; e += blockDim.x) {
                     int r = e / L;
                     const int ln = e % L;
-                    const bool rl = r < ci.n_rows;
-                    if (!rl) r = ci.n_rows - 1;
+                    const bool rl = r < ci.n_crows;
+                    if (!rl) r = ci.n_crows - 1;
                     const int inf = rinfo[r];
                     // slot-major [set][slot][row_pad]: the lanes of a warp read
                     // consecutive rows of one slot
@@ -596,11 +654,24 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
                                 const T th = halo[(size_t)(inf & 0xffff) * 4 + 2];
                                 b = a.gconst * th / (a.cp_tb2 + a.cp_tb2 / a.theta_bar * th);
                             }
-                            res[f * ci.n_rows + r] = b - acc;
+                            if (a.own_rows) a.resg[f * a.ng + ogp[r]] = b - acc;
+                            else res[f * ci.n_rows + r] = b - acc;
                         }
                     }
                 }
                 __syncthreads();
+            }
+            if (a.own_rows && (ci.n_rows > 0 || ci.n_crows > 0)) {
+                // ---- the band rows' residuals, formed by the CTAs owning their
+                // wall nodes, once every CTA that forms or reads them is here
+                if (!group_barrier(a.arrive2, a.abort, target2, (unsigned)a.wall_ctas, a.spin_limit)) return;
+                for (int e = threadIdx.x; e < 4 * ci.n_rows; e += blockDim.x) {
+                    const int f = e / ci.n_rows, k = e % ci.n_rows;
+                    res[e] = __ldcg(a.resg + f * a.ng + brow[k]);
+                }
+                __syncthreads();
+            }
+            if (ci.n_rows > 0) {
                 // ---- ghost values from the banded inverse rows -------------------
                 // M lanes per (ghost, class) pair, every field of the class at once
                 const int M = lanes_for(ci.n_gc, blockDim.x, kPairLanes);
@@ -637,6 +708,10 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
                                 halo[(size_t)gc.x * 4 + f] = f == 0 ? s0 : f == 1 ? s1 : f == 2 ? s2 : s3;
                     }
                 }
+                __syncthreads();
+            }
+            if (ci.n_rows > 0 || ci.n_crows > 0) {
+                cp_async_wait_pending<0>();   // the rest of the list (no-op at the first stage)
                 __syncthreads();
             }
             if constexpr (MLP) {
@@ -795,6 +870,12 @@ PArgs<T> pargs(Problem &pb, T *U, double dt, int64_t n_steps) {
     a.n_steps = n_steps;
     a.arrive = ps.arrive.p;
     a.base = ps.base;
+    a.own_rows = ps.own_rows ? 1 : 0;
+    a.wall_ctas = ps.wall_ctas;
+    a.ng = pb.gh.n_ghost > 0 ? pb.gh.rows : 0;
+    a.resg = (T *)ps.resg.p;
+    a.arrive2 = ps.arrive2.p;
+    a.base2 = ps.base2;
     a.abort = ps.abort.p;
     a.spin_limit = ps.spin_limit;
     return a;
@@ -975,7 +1056,18 @@ bool persistent_plan(Problem &pb, int G, int ctas) {
     std::vector<unsigned char> pwp((size_t)4 * SLQ * lanes * GV * ts, 0);
     const int64_t tot_old = (int64_t)SLQ * P * GV;
     const int64_t tot_new = (int64_t)SLQ * lanes * GV;
-    std::vector<int32_t> stamp(pb.n_all, -1), loc(pb.n_all, 0);
+    std::vector<int32_t> stamp(pb.n_all, -1), loc(pb.n_all, 0), wstamp(pb.n_all, -1);
+    // owned-rows mode (FP64): each wall row's residual is formed by the CTA
+    // owning its wall node (the rows' positions, per CTA, ascending)
+    const bool own = pb.precision == 64 && ng > 0;
+    std::vector<std::vector<int32_t>> orows_of(own ? grid : 0);
+    if (own) {
+        std::vector<int32_t> blk(P, -1);
+        for (int c = 0; c < grid; ++c)
+            for (size_t k = blocks[c].first; k < blocks[c].second; ++k) blk[ids[k]] = c;
+        for (int64_t rp = 0; rp < ng; ++rp) orows_of[blk[owner[at[rp]]]].push_back((int32_t)rp);
+    }
+    int wall_ctas = 0;
     std::vector<int32_t> rstamp(ng, -1), rloc(ng, 0);
     int halo_max = 0, rows_max = 0;
     size_t smem_max = 0;
@@ -1012,18 +1104,30 @@ bool persistent_plan(Problem &pb, int G, int ctas) {
         }
         std::sort(rows.begin(), rows.end());
         for (size_t k = 0; k < rows.size(); ++k) rloc[rows[k]] = (int32_t)k;
-        for (int32_t rp : rows) {
+        // the rows whose residuals it forms: its band rows, or its own rows
+        const std::vector<int32_t> &crows = own ? orows_of[c] : rows;
+        for (int32_t rp : crows) {
             const int32_t r = at[rp];
             for (int k = 0; k < npad; ++k) add(gidx[(int64_t)r * npad + k]);
             add(owner[r]);
         }
         std::sort(other.begin(), other.end());
         std::sort(ghosts.begin(), ghosts.end());
+        // records its wall rows read (row slots and owners) first among the
+        // others: they are copied as a group of their own
+        for (int32_t rp : crows) {
+            const int32_t r = at[rp];
+            for (int k = 0; k < npad; ++k) wstamp[gidx[(int64_t)r * npad + k]] = c;
+            wstamp[owner[r]] = c;
+        }
+        const auto wmid = std::stable_partition(other.begin(), other.end(), [&](int32_t j) { return wstamp[j] == c; });
+        const int n_wload = (int)(wmid - other.begin());
         const int n_list = n_own + (int)other.size() + (int)ghosts.size();
         if (n_list > 65535) return false;
         ci.list_off = (int32_t)hlist.size();
         ci.n_own = n_own;
         ci.n_load = n_own + (int)other.size();
+        ci.n_wload = n_wload;
         ci.n_list = n_list;
         for (int li = 0; li < n_own; ++li) hlist.push_back(ids[b0 + li]);
         for (size_t k = 0; k < other.size(); ++k) {
@@ -1051,17 +1155,20 @@ bool persistent_plan(Problem &pb, int G, int ctas) {
         }
 
         // ghost block: row slots, weight sets, row info, pairs, band coefficients
-        const int n_rows = (int)rows.size();
+        const int n_rows = (int)rows.size(), n_crows = (int)crows.size();
         ci.n_rows = n_rows;
+        ci.n_crows = n_crows;
         ci.blob_off = (int64_t)blob.size();
         rows_max = std::max(rows_max, n_rows);
+        if (n_crows > 0 && n_rows == 0) return false;   // a wall node whose stencil reads no ghost
+        if (n_rows > 0) ++wall_ctas;
         if (n_rows > 0) {
-            // distinct weight sets of each row (fields with the same boundary operator share one)
-            std::vector<std::vector<int>> setof(n_rows, std::vector<int>(4, 0));
-            std::vector<std::vector<int>> sets(n_rows);
+            // distinct weight sets of each formed row (fields with the same boundary operator share one)
+            std::vector<std::vector<int>> setof(n_crows, std::vector<int>(4, 0));
+            std::vector<std::vector<int>> sets(n_crows);
             int n_set = 1;
-            for (int k = 0; k < n_rows; ++k) {
-                const int32_t r = at[rows[k]];
+            for (int k = 0; k < n_crows; ++k) {
+                const int32_t r = at[crows[k]];
                 for (int f = 0; f < 4; ++f) {
                     const unsigned char *wf = gwv.data() + ((size_t)f * ng + r) * npad * ts;
                     int found = -1;
@@ -1080,15 +1187,15 @@ bool persistent_plan(Problem &pb, int G, int ctas) {
             ci.n_set = n_set;
             // row stride: the L lane groups of a warp (32 / L consecutive rows
             // each) start 32 / L banks apart
-            const int L = lanes_for(n_rows, threads, kRowLanes);
-            int RP = n_rows;
+            const int L = lanes_for(std::max(n_crows, 1), threads, kRowLanes);
+            int RP = std::max(n_crows, 1);
             while (RP % 32 != (32 / L) % 32) ++RP;
             ci.row_pad = RP;
             std::vector<unsigned char> b;
             std::vector<uint16_t> rs((size_t)npad * RP, 0);
-            std::vector<int32_t> ri(n_rows);
-            for (int k = 0; k < n_rows; ++k) {
-                const int32_t r = at[rows[k]];
+            std::vector<int32_t> ri(n_crows);
+            for (int k = 0; k < n_crows; ++k) {
+                const int32_t r = at[crows[k]];
                 for (int t = 0; t < npad; ++t) rs[(size_t)t * RP + k] = (uint16_t)loc[gidx[(int64_t)r * npad + t]];
                 ri[k] = loc[owner[r]] | (tbv[r] ? 1 << 16 : 0) | (setof[k][0] << 17) | (setof[k][1] << 19) |
                         (setof[k][2] << 21) | (setof[k][3] << 23);
@@ -1096,8 +1203,8 @@ bool persistent_plan(Problem &pb, int G, int ctas) {
             put(b, 0, rs.data(), rs.size() * 2);
             ci.o_rw = (int32_t)align16(b.size());
             b.resize(ci.o_rw + (size_t)n_set * npad * RP * ts, 0);
-            for (int k = 0; k < n_rows; ++k) {
-                const int32_t r = at[rows[k]];
+            for (int k = 0; k < n_crows; ++k) {
+                const int32_t r = at[crows[k]];
                 for (size_t s = 0; s < sets[k].size(); ++s)
                     for (int t = 0; t < npad; ++t)
                         put(b, ci.o_rw + (((size_t)s * npad + t) * RP + k) * ts,
@@ -1105,6 +1212,11 @@ bool persistent_plan(Problem &pb, int G, int ctas) {
             }
             ci.o_rinfo = (int32_t)align16(b.size());
             put(b, ci.o_rinfo, ri.data(), ri.size() * 4);
+            // global positions of the formed rows and of the band rows (owned-rows mode)
+            ci.o_ogp = (int32_t)align16(b.size());
+            put(b, ci.o_ogp, crows.data(), crows.size() * 4);
+            ci.o_brow = (int32_t)align16(b.size());
+            put(b, ci.o_brow, rows.data(), rows.size() * 4);
             // (ghost, class) pairs and their band coefficients, pair-interleaved
             // [coefficient j][pair_pad] with the lane groups of a warp in distinct banks
             std::vector<std::pair<int32_t, int32_t>> pairs;   // (ghost record, class)
@@ -1200,6 +1312,14 @@ bool persistent_plan(Problem &pb, int G, int ctas) {
     if (ps.arrive.n == 0) ps.arrive.alloc(1);
     RBF_CUDA(cudaMemset(ps.arrive.p, 0, sizeof(unsigned)));
     ps.base = 0;
+    ps.own_rows = own;
+    ps.wall_ctas = wall_ctas;
+    if (own) {
+        ps.resg.alloc(std::max<size_t>((size_t)4 * ng * ts, 16));
+        if (ps.arrive2.n == 0) ps.arrive2.alloc(1);
+        RBF_CUDA(cudaMemset(ps.arrive2.p, 0, sizeof(unsigned)));
+        ps.base2 = 0;
+    }
     if (ps.abort.n == 0) {
         ps.abort.alloc(1);
         RBF_CUDA(cudaMemset(ps.abort.p, 0, sizeof(int)));
@@ -1223,8 +1343,10 @@ void persistent_run(Problem &pb, double dt, int64_t n_steps, void *U, cudaStream
         void *args[] = {&a};
         RBF_CUDA(cudaLaunchCooperativeKernel(fn, dim3(ps.grid), dim3(ps.threads), args, ps.smem, s));
     }
-    // one barrier after every stage but the last
+    // one barrier after every stage but the last; in owned-rows mode one
+    // barrier of the ghost-solving CTAs in every stage
     ps.base += (unsigned)((uint64_t)ps.grid * (uint64_t)(4 * n_steps - 1));
+    if (ps.own_rows) ps.base2 += (unsigned)((uint64_t)ps.wall_ctas * (uint64_t)(4 * n_steps));
 }
 
 bool persistent_mlp_ready(const Problem &pb) {
@@ -1287,6 +1409,8 @@ void persistent_check(Problem &pb) {
         // an aborted launch left the arrival count unknown: restart it
         RBF_CUDA(cudaMemset(pb.ps.arrive.p, 0, sizeof(unsigned)));
         pb.ps.base = 0;
+        if (pb.ps.arrive2.n) RBF_CUDA(cudaMemset(pb.ps.arrive2.p, 0, sizeof(unsigned)));
+        pb.ps.base2 = 0;
         RBF_CUDA(cudaMemset(pb.ps.abort.p, 0, sizeof(int)));
         RBF_FAIL(RBF_E_TIMEOUT,
                  "a grid barrier of the persistent kernel gave up after %lld polls; the state is partially "

@@ -82,6 +82,14 @@ struct PersistPlan {
     DevBuf<unsigned int> arrive; // barrier arrivals, monotone across launches
     unsigned base = 0;           // its value when the next launch starts
     DevBuf<int> abort;           // set when a barrier wait gives up (sticky until rbf_sync)
+    // owned-rows mode (FP64): each wall row's residual is formed once, by the
+    // CTA that owns its wall node, and read back from global memory by the
+    // CTAs that solve ghosts after a barrier among those CTAs only
+    bool own_rows = false;
+    int wall_ctas = 0;           // CTAs that solve ghosts (the barrier's members)
+    DevBuf<unsigned char> resg;  // T [4][ghost rows] residuals of the stage
+    DevBuf<unsigned int> arrive2;   // their barrier's arrivals
+    unsigned base2 = 0;
     long long spin_limit = 1LL << 21;   // polls per barrier wait (about a second)
 };
 
