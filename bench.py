@@ -685,7 +685,7 @@ def ensemble_case(torch, args):
     ach = bpl / (avg / 1e3) / 1e9
     out = {"workload": f"{len(every)} density-current members, {ens.n_prog} nodes + {ens.n_all - ens.n_prog} ghosts "
                        f"on this rank ({len(members)} members), h in 50-400 m, cart/hex/scattered, n 31-75 "
-                       f"(Cartesian without n=31 l=3 and n=75 l=5), FP32",
+                       f"(Cartesian without n=75 l=5; Cartesian n=31 l=3 with hyperviscosity constant 2^-5), FP32",
            "value": upd / (ms / 1e3), "unit": "node-updates/s", "node_rhs_per_s": 4.0 * upd / (ms / 1e3),
            "scaling": "strong", "ranks": world, "members_per_rank": len(members),
            "timed_global_steps": K, "ms": ms, "node_updates_to_900s": sum_over_ranks(ens.node_updates(-1), world),

@@ -246,6 +246,8 @@ typedef struct rbf_ens_member {
     int64_t n_steps;        /* steps to its end time                              */
     double spacing;         /* its node spacing h: with common.gamma_c > 0 its
                                gamma is common.gamma_c * spacing^(2 hv_k - 1)    */
+    double gamma_c;         /* > 0: its own hyperviscosity constant in place of
+                               common.gamma_c (0: the common one)                */
 } rbf_ens_member;
 
 /*

@@ -450,9 +450,10 @@ void build_ensemble(Problem &pb, const rbf_ns_params &common, int n, const rbf_e
         p.n_sten = mr.n_sten;
         p.poly_l = mr.poly_l;
         p.period_x = mr.period_x;
-        // each member's own gamma: common.gamma_c with the member's spacing,
-        // or the member's gamma as given
-        p.gamma = resolve_gamma(mr.gamma, common.gamma_c, mr.spacing, common.hv_k);
+        // each member's own gamma: its own constant (or the common one) with
+        // the member's spacing, or the member's gamma as given
+        RBF_REQUIRE(std::isfinite(mr.gamma_c) && mr.gamma_c >= 0.0, "member %d: gamma_c must be >= 0", r);
+        p.gamma = resolve_gamma(mr.gamma, mr.gamma_c > 0.0 ? mr.gamma_c : common.gamma_c, mr.spacing, common.hv_k);
         p.gamma_c = 0.0;
         p.threads_per_node = 2;
         std::unique_ptr<Problem> m(new Problem());

@@ -45,7 +45,7 @@ class AdvParams(C.Structure):
 class EnsMember(C.Structure):
     _fields_ = [("n_prog", C.c_int64), ("n_all", C.c_int64), ("n_sten", C.c_int32), ("poly_l", C.c_int32),
                 ("period_x", C.c_double), ("gamma", C.c_double), ("dt", C.c_double), ("n_steps", C.c_int64),
-                ("spacing", C.c_double)]
+                ("spacing", C.c_double), ("gamma_c", C.c_double)]
 
 
 class Info(C.Structure):
@@ -438,7 +438,7 @@ def ensemble_problem(members, precision=32, p=7, hv_k=3, mu=75.0, gamma_c=2.0 **
     for r, m in enumerate(members):
         arr[r] = EnsMember(n_prog=m.nodes.n_prog, n_all=m.nodes.n_all, n_sten=m.n, poly_l=m.l,
                            period_x=m.nodes.period_x, gamma=0.0, dt=m.dt, n_steps=m.n_steps,
-                           spacing=m.nodes.h)
+                           spacing=m.nodes.h, gamma_c=getattr(m, "gamma_c", 0.0) or 0.0)
     x = np.ascontiguousarray(np.concatenate([m.nodes.x for m in members]), np.float64)
     z = np.ascontiguousarray(np.concatenate([m.nodes.z for m in members]), np.float64)
     kind = np.ascontiguousarray(np.concatenate([m.nodes.kind for m in members]), np.int32)

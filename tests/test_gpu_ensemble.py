@@ -56,7 +56,8 @@ def test_ensemble_fp64_matches_oracle_per_member():
     assert ens.node_updates() == sum(m.nodes.n_prog * m.n_steps for m in mem)
     for r, m in enumerate(mem):
         P = m.nodes.n_prog
-        ref, s = fb.with_spread(lambda order: NSOracle(m.nodes, n=m.n, l=m.l, stencil_order=order, workers=WORKERS),
+        ref, s = fb.with_spread(lambda order: NSOracle(m.nodes, n=m.n, l=m.l, gamma_c=m.gamma_c, stencil_order=order,
+                                                                workers=WORKERS),
                                 lambda o: o.run(m.U0, 0.0, m.dt, m.n_steps)[:, :P])
         got = ens.member_fields(U, r)
         fb.check(got[:, :P], ref, s, f"member {r} ({m.nodes.layout}, h={m.nodes.h:g}, n={m.n}, steps={m.n_steps})")
@@ -70,7 +71,7 @@ def test_ensemble_fp32_equals_members_stepped_alone():
     ens.run(-1, U)
     ens.sync()
     for r, m in enumerate(mem):
-        pb = rbffd.ns_problem(m.nodes, precision=32, n=m.n, l=m.l, threads_per_node=G)
+        pb = rbffd.ns_problem(m.nodes, precision=32, n=m.n, l=m.l, gamma_c=m.gamma_c, threads_per_node=G)
         V = rbffd.state_tensor(m.U0, 32)
         pb.run(0.0, m.dt, m.n_steps, V)
         pb.sync()
@@ -120,3 +121,22 @@ def test_coarse_draw_runs_to_900s_finite():
     ens.sync()
     bad = [r for r, m in enumerate(mem) if not np.all(np.isfinite(ens.member_fields(U, r)[:, :m.nodes.n_prog]))]
     assert not bad, [(r, mem[r].nodes.h, mem[r].nodes.layout, mem[r].n, mem[r].l) for r in bad]
+
+
+def test_cartesian_31_3_member_runs_to_900s_with_its_constant():
+    """The Cartesian n = 31, l = 3 member at 50 m (the finest spacing of the
+    draw), batched with a hexagonal member: with its own hyperviscosity
+    constant 2^-5 (inputs.ENSEMBLE_GAMMA_C) both run to 900 s finite in FP32;
+    with the common 2^-6 it goes non-finite near 630 s."""
+    mem = [inp.density_current_member(50.0, "cart", 31, 3, seed=31),
+           inp.density_current_member(400.0, "hex", 37, 4, seed=32)]
+    assert mem[0].gamma_c == 2.0 ** -5 and mem[1].gamma_c == 2.0 ** -6
+    ens = rbffd.ensemble_problem(mem, precision=32)
+    U = ens.state()
+    ens.run(-1, U)
+    ens.sync()
+    mm = ens.minmax(U)
+    print("Cartesian (31,3) 50 m + hex 400 m to 900 s: theta' [%.3f, %.3f], w [%.2f, %.2f]"
+          % (mm[2, 0], mm[2, 1], mm[1, 0], mm[1, 1]))
+    assert np.all(np.isfinite(mm))
+

@@ -157,7 +157,7 @@ def test_ensemble_lattice_matches_per_node(prec):
             assert max(errs) < 1e-5, (r, errs)
             continue
         P = m.nodes.n_prog
-        ref, s = fb.with_spread(lambda order: NSOracle(m.nodes, n=m.n, l=m.l, stencil_order=order),
+        ref, s = fb.with_spread(lambda order: NSOracle(m.nodes, n=m.n, l=m.l, gamma_c=m.gamma_c, stencil_order=order),
                                 lambda o: o.run(m.U0, 0.0, m.dt, m.n_steps)[:, :P])
         # the two storages differ by the rounding of translated stencils' weights
         assert np.all(np.array(errs) < fb.bound(s)), (r, errs, s)
