@@ -635,12 +635,13 @@ def large_case(torch, args, flush):
 
 
 def _time_ensemble(torch, ens, K, nvtx):
-    """Node-updates/s of K global RK4 steps (after 3 untimed) and the median
-    stage-kernel time of 3 more, for an ensemble's initial state; ``nvtx``
-    names an NVTX range around the K timed steps."""
+    """Node-updates/s of K global RK4 steps (after K untimed ones, which also
+    build the run's graph) and the median stage-kernel time of 3 more, for an
+    ensemble's initial state; ``nvtx`` names an NVTX range around the K timed
+    steps."""
     U = ens.state()
     stream = torch.cuda.current_stream()
-    ens.run(3, U)
+    ens.run(K, U)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push(nvtx)

@@ -505,8 +505,116 @@ void build_ensemble(Problem &pb, const rbf_ns_params &common, int n, const rbf_e
     RBF_CUDA(cudaStreamSynchronize(pb.st));
 }
 
+namespace {
+
+// One pass of a whole-run graph's loop: the WHILE node that repeats a phase's
+// chunk of steps stops once its counter reaches zero.
+__global__ void count_down(unsigned *counter, cudaGraphConditionalHandle h) {
+    if (threadIdx.x == 0) {
+        const unsigned v = *counter - 1;
+        *counter = v;
+        if (v == 0) cudaGraphSetConditional(h, 0);
+    }
+}
+
+constexpr int kRunChunk = 16;   // steps per loop pass of a phase
+
+// Captures a whole run of `total` global steps as one graph: per phase of
+// constant active prefix (members leave it as they reach their end), a memset
+// that arms the phase's counter, a WHILE node whose body is kRunChunk steps of
+// the active members and the count-down kernel, then the phase's leftover
+// steps.  The loop bodies hold plain kernel launches (no programmatic
+// dependent launch edges).
+void build_run_graph(Problem &pb, int64_t total, void *U) {
+    EnsembleState &E = *pb.ens;
+    if (pb.graph) cudaGraphExecDestroy(pb.graph);
+    pb.graph = nullptr;
+    std::vector<std::pair<int, int64_t>> phases;   // (active members, steps)
+    for (int64_t t = 0; t < total;) {
+        int active = 0;
+        while (active < (int)E.order.size() && E.n_steps[E.order[active]] > t) ++active;
+        const int64_t phase_end = std::min(total, E.n_steps[E.order[active - 1]]);
+        phases.emplace_back(active, phase_end - t);
+        t = phase_end;
+    }
+    if (E.wcount.n < phases.size()) E.wcount.alloc(phases.size());
+    const bool pdl0 = pb.pdl;
+    pb.pdl = false;
+    cudaGraph_t g = nullptr;
+    RBF_CUDA(cudaGraphCreate(&g, 0));
+    bool capturing = false;
+    try {
+        std::vector<cudaGraphNode_t> deps;
+        for (size_t p = 0; p < phases.size(); ++p) {
+            E.active_members = phases[p].first;
+            const int64_t steps = phases[p].second;
+            const int chunk = (int)std::min<int64_t>(steps, kRunChunk);
+            const int64_t passes = steps / chunk, rem = steps - passes * chunk;
+            cudaMemsetParams mp = {};
+            mp.dst = E.wcount.p + p;
+            mp.value = (unsigned)passes;
+            mp.elementSize = 4;
+            mp.width = 1;
+            mp.height = 1;
+            cudaGraphNode_t arm;
+            RBF_CUDA(cudaGraphAddMemsetNode(&arm, g, deps.data(), deps.size(), &mp));
+            cudaGraphConditionalHandle h;
+            RBF_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t loop;
+            RBF_CUDA(cudaGraphAddNode(&loop, g, &arm, nullptr, 1, &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            RBF_CUDA(cudaStreamBeginCaptureToGraph(pb.cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            capturing = true;
+            for (int q = 0; q < chunk; ++q) enqueue_ens_step(pb, 0.0, U, pb.cap, false, q);
+            count_down<<<1, 32, 0, pb.cap>>>(E.wcount.p + p, h);
+            RBF_CHECK_LAUNCH();
+            cudaGraph_t out = nullptr;
+            capturing = false;
+            RBF_CUDA(cudaStreamEndCapture(pb.cap, &out));
+            deps.assign(1, loop);
+            if (rem > 0) {
+                RBF_CUDA(cudaStreamBeginCaptureToGraph(pb.cap, g, deps.data(), nullptr, deps.size(),
+                                                       cudaStreamCaptureModeThreadLocal));
+                capturing = true;
+                for (int q = 0; q < rem; ++q) enqueue_ens_step(pb, 0.0, U, pb.cap, false, q);
+                cudaStreamCaptureStatus cs;
+                const cudaGraphNode_t *tail = nullptr;
+                size_t nt = 0;
+                RBF_CUDA(cudaStreamGetCaptureInfo(pb.cap, &cs, nullptr, nullptr, &tail, nullptr, &nt));
+                std::vector<cudaGraphNode_t> next(tail, tail + nt);
+                capturing = false;
+                RBF_CUDA(cudaStreamEndCapture(pb.cap, &out));
+                deps = next;
+            }
+        }
+        RBF_CUDA(cudaGraphInstantiate(&pb.graph, g, 0));
+    } catch (...) {
+        if (capturing) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(pb.cap, &junk);
+        }
+        cudaGraphDestroy(g);
+        pb.pdl = pdl0;
+        throw;
+    }
+    cudaGraphDestroy(g);
+    pb.pdl = pdl0;
+    pb.graph_U = U;
+    pb.graph_steps = (int)std::min<int64_t>(total, INT32_MAX);
+    E.whole_run = true;
+}
+
+}  // namespace
+
 // Steps every member min(max_steps, its n_steps) steps (max_steps < 0: all).
-// Phases of constant active prefix are replayed from captured graphs.
+// The whole run is one graph launch (build_run_graph, rebuilt when the state
+// or the step count changes); with stage timing on, phases are replayed from
+// one-step graphs that carry the timing events instead.
 void run_ensemble(Problem &pb, int64_t max_steps, void *U) {
     EnsembleState &E = *pb.ens;
     RBF_REQUIRE(U != nullptr, "null state");
@@ -516,16 +624,22 @@ void run_ensemble(Problem &pb, int64_t max_steps, void *U) {
     RBF_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     RBF_CUDA(cudaEventRecord(ev, pb.st));
     RBF_CUDA(cudaStreamWaitEvent(pb.cap, ev, 0));
-    int64_t t = 0;
+    if (!pb.record_rhs_events && total > 0) {
+        if (!pb.graph || !E.whole_run || pb.graph_U != U || pb.graph_steps != (int)std::min<int64_t>(total, INT32_MAX))
+            build_run_graph(pb, total, U);
+        RBF_CUDA(cudaGraphLaunch(pb.graph, pb.cap));
+    }
+    int64_t t = pb.record_rhs_events ? 0 : total;
     while (t < total) {
         int active = 0;
         while (active < (int)E.order.size() && E.n_steps[E.order[active]] > t) ++active;
         const int64_t phase_end = std::min(total, E.n_steps[E.order[active - 1]]);
         const int64_t steps = phase_end - t;
         const int chunk = (int)std::min<int64_t>(steps, pb.record_rhs_events ? 1 : 16);
-        if (!pb.graph || pb.graph_U != U || pb.graph_steps != chunk || E.active_members != active) {
+        if (!pb.graph || E.whole_run || pb.graph_U != U || pb.graph_steps != chunk || E.active_members != active) {
             if (pb.graph) cudaGraphExecDestroy(pb.graph);
             pb.graph = nullptr;
+            E.whole_run = false;
             E.active_members = active;
             if (pb.record_rhs_events) {
                 for (cudaEvent_t e : pb.rhs_ev) cudaEventDestroy(e);

@@ -27,6 +27,8 @@ struct EnsembleState {
     DevBuf<unsigned char> descs;        // one block descriptor per stage block
     int64_t total_records = 0, total_nodes = 0;
     int active_members = 0;             // launch geometry of the captured graph
+    bool whole_run = false;             // the captured graph is a whole run (loop nodes)
+    DevBuf<unsigned> wcount;            // loop counters of the whole-run graph, one per phase
 };
 
 struct GhostPlan {

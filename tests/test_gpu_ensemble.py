@@ -140,3 +140,26 @@ def test_cartesian_31_3_member_runs_to_900s_with_its_constant():
           % (mm[2, 0], mm[2, 1], mm[1, 0], mm[1, 1]))
     assert np.all(np.isfinite(mm))
 
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_whole_run_is_one_graph_launch_equal_to_phase_replay(precision):
+    """rbf_ens_run without stage timing runs the whole ensemble as one CUDA
+    graph launch (a device-side WHILE loop per phase of constant active
+    prefix, leftover steps after it); with stage timing it replays one-step
+    graphs per phase.  Members of uneven step counts (20, 40 and 45 steps,
+    so the phases have leftover steps) end bitwise equal on both paths."""
+    mem = [inp.density_current_member(800.0, "hex", 37, 4, seed=41, t_end=40.0),
+           inp.density_current_member(400.0, "cart", 45, 4, seed=42, t_end=40.0),
+           inp.density_current_member(400.0, "scattered", 37, 4, seed=43, t_end=45.0)]
+    assert sorted(m.n_steps for m in mem) == [20, 40, 45]
+    ens = rbffd.ensemble_problem(mem, precision=precision)
+    A = ens.state()
+    ens.run(-1, A)
+    B = ens.state()
+    ens.set_stage_timing(True)
+    ens.run(-1, B)
+    ens.set_stage_timing(False)
+    ens.sync()
+    assert torch.equal(A, B)
+    assert torch.all(torch.isfinite(A))
+
