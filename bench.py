@@ -638,7 +638,8 @@ def _time_ensemble(torch, ens, K, nvtx):
     """Node-updates/s of K global RK4 steps (after K untimed ones, which also
     build the run's graph) and the median stage-kernel time of 3 more, for an
     ensemble's initial state; ``nvtx`` names an NVTX range around the K timed
-    steps."""
+    steps and ``nvtx + "_stages"`` one around the 3 stage-timed steps (plain
+    kernel launches, which an ncu capture can select)."""
     U = ens.state()
     stream = torch.cuda.current_stream()
     ens.run(K, U)
@@ -653,9 +654,11 @@ def _time_ensemble(torch, ens, K, nvtx):
     ms = e0.elapsed_time(e1)
     ens.set_stage_timing(True)
     stage = []
+    torch.cuda.nvtx.range_push(nvtx + "_stages")
     for _ in range(3):
         ens.run(1, U)
         stage.append(ens.stage_kernel_ms() / 4.0)
+    torch.cuda.nvtx.range_pop()
     ens.set_stage_timing(False)
     mm = ens.minmax(U)
     return ms, float(np.median(stage)), bool(np.all(np.isfinite(mm))), U
