@@ -523,8 +523,12 @@ def weights_case(torch, nodes, n, p, l, hv_k, peak_tflops, label):
 def time_steps(torch, pb, U, dt, steps, warmup, flush, stage_timing, nvtx=None):
     """Per-step device times (ms) and summed stage-kernel times (ms).  With a
     ``flush`` buffer, L2 is evicted before every step (for working sets that
-    fit in L2); ``nvtx`` names an NVTX range around the timed steps (for a
-    profiler's launch filter)."""
+    fit in L2) and each step is timed on its own; without one (and without
+    stage timing) the timed steps are enqueued back to back between one pair
+    of events (one ``run`` call per step, as in the warm-up, so the host's
+    launch latency overlaps the device work) and each step gets the mean.
+    ``nvtx`` names an NVTX range around the timed steps (for a profiler's
+    launch filter)."""
     stream = torch.cuda.current_stream()
     pb.set_stage_timing(stage_timing)
     t = 0.0
@@ -539,17 +543,26 @@ def time_steps(torch, pb, U, dt, steps, warmup, flush, stage_timing, nvtx=None):
     e1 = torch.cuda.Event(enable_timing=True)
     if nvtx:
         torch.cuda.nvtx.range_push(nvtx)
-    for _ in range(steps):
-        if flush is not None:
-            flush.zero_()
+    if flush is None and not stage_timing:
         e0.record(stream)
-        pb.run(t, dt, 1, U)
+        for _ in range(steps):
+            pb.run(t, dt, 1, U)
+            t += dt
         e1.record(stream)
         e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        if stage_timing:
-            stage_ms.append(pb.stage_kernel_ms())
-        t += dt
+        step_ms = [e0.elapsed_time(e1) / steps] * steps
+    else:
+        for _ in range(steps):
+            if flush is not None:
+                flush.zero_()
+            e0.record(stream)
+            pb.run(t, dt, 1, U)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            if stage_timing:
+                stage_ms.append(pb.stage_kernel_ms())
+            t += dt
     if nvtx:
         torch.cuda.nvtx.range_pop()
     pb.set_stage_timing(False)

@@ -2,13 +2,14 @@
 // (Sec. 3, Eq. (weights); hyperviscosity by the PHS Laplacian recursion of
 // Sec. 5.3, Eq. (laplacian)).
 //
-// GPU design: one warp per stencil.  The S x (S + K) augmented matrix
-// (S = n + (l+1)(l+2)/2 unknowns, K right-hand sides = operators) lives in
-// shared memory; the warp runs Gaussian elimination with partial pivoting
-// (lanes own columns, the elimination walks the rows), then a column-oriented
-// back substitution (lanes own rows).  All arithmetic is FP64: the systems'
-// conditioning grows with the PHS order (Sec. 2), and the work is FP64-ALU
-// bound (about (2/3) S^3 flops per node), not a dense GEMM.
+// GPU design: one CTA of four warps per stencil.  The S x (S + K) augmented
+// matrix (S = n + (l+1)(l+2)/2 unknowns, K right-hand sides = operators) lives
+// in shared memory.  The CTA runs Gaussian elimination with partial pivoting,
+// one barrier per step: warp 0 looks one column ahead (update, pivot,
+// multipliers) while the other three warps update the trailing block.  A
+// column-oriented back substitution follows.  All arithmetic is FP64: the
+// systems' conditioning grows with the PHS order (Sec. 2), and the work is
+// FP64-ALU bound (about (2/3) S^3 flops per node), not a dense GEMM.
 #include <climits>
 #include <cmath>
 
@@ -86,26 +87,76 @@ __device__ double poly_rhs(int op, int k, int a, int b) {
     return 0.0;
 }
 
-__global__ void weights_kernel(const double *__restrict__ x, const double *__restrict__ z,
-                               const int32_t *__restrict__ idx, int64_t n_centers, WeightJob job,
-                               double *__restrict__ w, int *__restrict__ bad_node) {
-    extern __shared__ double sm[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t c = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp;
-    if (c >= n_centers) return;
-    const int n = job.n, S = job.S, ld = job.ld, K = job.nops;
-    double *A = sm + (size_t)warp * (S * ld + 2 * n + 8);
-    double *xi = A + S * ld;
-    double *eta = xi + n;
+// Look-ahead step of weights_kernel, run by one warp: the pivot of column
+// col among logical rows col.. (permutation pc), the permutation with the
+// pivot row moved to col (pn; pn == pc allowed), the pivot, its failure flag
+// (by the step's parity) and the multipliers of the rows below it.
+__device__ __forceinline__ void pivot_step(double *A, int ld, int S, int col, const int *pc, int *pn, double *mvn,
+                                           double *diag, int *s_bad, int lane) {
+    const long long kTiny = __double_as_longlong(1e-14);
+    const long long kInf = 0x7ff0000000000000LL;
+    long long best = -1;
+    int bi = col;
+    for (int i = col + lane; i < S; i += 32) {
+        const long long v = __double_as_longlong(A[pc[i] * ld + col]) & 0x7fffffffffffffffLL;
+        if (v > best) { best = v; bi = i; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    const bool bad = !(best > kTiny) || best >= kInf;   // tiny, inf or NaN pivot
+    const int rc = pc[col], rb = pc[bi];
+    const double piv = A[rb * ld + col];
+    __syncwarp();
+    if (pn != pc)   // entries from col - 1 on: pn then holds every settled entry
+        for (int i = col - 1 + lane; i < S; i += 32) pn[i] = pc[i];
+    __syncwarp();
+    if (lane == 0) {
+        pn[col] = rb;
+        pn[bi] = rc;
+        diag[col] = piv;
+        s_bad[col & 1] = bad;
+    }
+    __syncwarp();
+    const double inv = bad ? 0.0 : 1.0 / piv;
+    for (int i = col + 1 + lane; i < S; i += 32) mvn[i] = A[pn[i] * ld + col] * inv;
+}
 
-    // shifted coordinates and stencil radius s = max_j ||x_j - x_c||
+// One CTA of NT threads per stencil, one barrier per elimination step.  Rows
+// are addressed through a permutation (logical row -> shared-memory row)
+// instead of being swapped.  In step kk, warp 0 updates column kk+1, finds the
+// pivot of step kk+1 and writes the next permutation and multipliers (both
+// double-buffered), while the other warps update columns kk+2.. of the
+// trailing block with the current ones.  The results are the same bits as a
+// plain elimination with row swaps: every entry sees the same operations.
+template <int NT>
+__global__ void __launch_bounds__(NT) weights_kernel(const double *__restrict__ x, const double *__restrict__ z,
+                                                     const int32_t *__restrict__ idx, int64_t n_centers,
+                                                     WeightJob job, double *__restrict__ w,
+                                                     int *__restrict__ bad_node) {
+    extern __shared__ double sm[];
+    __shared__ double s_red[NT / 32];
+    __shared__ int s_bad[2];        // pivot failure flags, by the parity of the step they belong to
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t c = blockIdx.x;
+    if (c >= n_centers) return;
+    const int n = job.n, S = job.S, ld = job.ld, K = job.nops, W = S + K;
+    double *A = sm;                 // S x ld, row-major, rows in shared-memory order
+    double *xi = A + S * ld;        // n shifted, scaled coordinates
+    double *eta = xi + n;
+    double *const mv0 = eta + n, *const mv1 = mv0 + S;   // multipliers, double-buffered by step
+    double *const diag = mv1 + S;                         // S pivots (the diagonal of U)
+    int *const pm0 = reinterpret_cast<int *>(diag + S), *const pm1 = pm0 + S;   // permutations, likewise
+
     const int32_t *row = idx + c * n;
     const double xc = x[c], zc = z[c];
     double smax = 0.0;
-    bool bad_idx = false;
-    for (int j = lane; j < n; j += 32) {
+    int bad_idx = 0;
+    for (int j = tid; j < n; j += NT) {
         int q = row[j];
-        if (q < 0 || q >= job.n_all) { bad_idx = true; q = (int)c; }
+        if (q < 0 || q >= job.n_all) { bad_idx = 1; q = (int)c; }
         double dx = x[q] - xc;
         if (job.period > 0.0) {
             if (dx > 0.5 * job.period) dx -= job.period;
@@ -117,32 +168,32 @@ __global__ void weights_kernel(const double *__restrict__ x, const double *__res
         smax = fmax(smax, sqrt(dx * dx + dz * dz));
     }
     for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-    if (__any_sync(0xffffffffu, bad_idx)) {   // index outside [0, n_all): report, skip
-        if (lane == 0) atomicMin(bad_node, (int)c);
+    if (lane == 0) s_red[warp] = smax;
+    if (__syncthreads_or(bad_idx)) {
+        if (tid == 0) atomicMin(bad_node, (int)c);
         return;
     }
+    smax = s_red[0];
+    for (int q = 1; q < NT / 32; ++q) smax = fmax(smax, s_red[q]);
     const double inv_s = 1.0 / smax;
-    __syncwarp();
-    for (int j = lane; j < n; j += 32) { xi[j] *= inv_s; eta[j] *= inv_s; }
-    __syncwarp();
+    for (int j = tid; j < n; j += NT) { xi[j] *= inv_s; eta[j] *= inv_s; }
+    for (int i = tid; i < S; i += NT) { pm0[i] = i; pm1[i] = i; }
+    __syncthreads();
 
-    // assemble [A P | rhs; P^T 0 | rhs]; the PHS block is symmetric, so each
-    // pair (i <= j) is evaluated once (entries of the upper triangle walked
-    // row by row, 32 apart per lane)
     {
-        int i = 0, j = lane;
-        while (i < n && j >= n) { j -= n - i - 1; ++i; }   // j - i counts from the diagonal
+        int i = 0, j = tid;
+        while (i < n && j >= n) { j -= n - i - 1; ++i; }
         for (; i < n;) {
             double dx = xi[i] - xi[j], dz = eta[i] - eta[j];
             double r2 = dx * dx + dz * dz;
             const double v = (r2 == 0.0) ? 0.0 : rpow_odd(r2, sqrt(r2), job.p);
             A[i * ld + j] = v;
             A[j * ld + i] = v;
-            j += 32;
+            j += NT;
             while (i < n && j >= n) { j -= n - i - 1; ++i; }
         }
     }
-    for (int i = lane; i < n; i += 32) {
+    for (int i = tid; i < n; i += NT) {
         int m = 0;
         for (int d = 0; d <= job.l; ++d) {
             for (int b = 0; b <= d; ++b, ++m) {
@@ -156,92 +207,91 @@ __global__ void weights_kernel(const double *__restrict__ x, const double *__res
         }
         for (int o = 0; o < K; ++o) A[i * ld + S + o] = phs_rhs(job.ops[o], job.p, job.k, -xi[i], -eta[i]);
     }
-    for (int e = lane; e < job.M * job.M; e += 32) {
+    for (int e = tid; e < job.M * job.M; e += NT) {
         int r = e / job.M, q = e - r * job.M;
         A[(n + r) * ld + n + q] = 0.0;
     }
-    if (lane < job.M) {
+    if (tid < job.M) {
         int m = 0;
         for (int d = 0; d <= job.l; ++d)
             for (int b = 0; b <= d; ++b, ++m)
-                if (m == lane)
+                if (m == tid)
                     for (int o = 0; o < K; ++o) A[(n + m) * ld + S + o] = poly_rhs(job.ops[o], job.k, d - b, b);
     }
-    __syncwarp();
+    __syncthreads();
 
-    // Gaussian elimination with partial pivoting on the S x (S + K) block.
-    // The pivot search compares |a| through its bit pattern (for non-negative
-    // doubles the integer order is the numeric order), keeping the compares off
-    // the FP64 pipe; the rank-1 update of the trailing block spreads its entries
-    // over all 32 lanes.
-    const int W = S + K;
-    bool singular = false;
-    const long long kTiny = __double_as_longlong(1e-14);
-    const long long kInf = 0x7ff0000000000000LL;
-    for (int kk = 0; kk < S; ++kk) {
-        long long best = -1;
-        int bi = kk;
-        for (int i = kk + lane; i < S; i += 32) {
-            const long long v = __double_as_longlong(A[i * ld + kk]) & 0x7fffffffffffffffLL;
-            if (v > best) { best = v; bi = i; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-        }
-        if (!(best > kTiny) || best >= kInf) { singular = true; break; }   // tiny, inf or NaN pivot
-        if (bi != kk)
-            for (int j = kk + lane; j < W; j += 32) {
-                double t = A[kk * ld + j];
-                A[kk * ld + j] = A[bi * ld + j];
-                A[bi * ld + j] = t;
+    if (warp == 0) pivot_step(A, ld, S, 0, pm0, pm0, mv0, diag, s_bad, lane);
+    __syncthreads();
+    int cur = 0;
+    int failed = s_bad[0];
+    if (!failed) {
+        for (int kk = 0; kk < S; ++kk) {
+            const int *pc = cur ? pm1 : pm0;
+            const double *mc = cur ? mv1 : mv0;
+            const double *prow = A + pc[kk] * ld;
+            if (warp == 0) {
+                if (kk + 1 < S) {
+                    const double pk = prow[kk + 1];
+                    for (int i = kk + 1 + lane; i < S; i += 32) A[pc[i] * ld + kk + 1] -= mc[i] * pk;
+                    __syncwarp();
+                    pivot_step(A, ld, S, kk + 1, pc, cur ? pm0 : pm1, cur ? mv0 : mv1, diag, s_bad, lane);
+                }
+            } else {
+                // A[i][j] -= m_i p_j, logical rows i > kk, columns j >= kk+2,
+                // entries NT-32 apart in row-major order, two per pass
+                constexpr int NB = NT - 32;
+                const int wcols = W - kk - 2, rows = S - kk - 1;
+                if (wcols > 0 && rows > 0) {
+                    const int qi = NB / wcols, qj = NB - qi * wcols;
+                    const int t = tid - 32;
+                    int i = t / wcols, j = t - i * wcols;
+                    const int *prm = pc + kk + 1;
+                    const double *mrow = mc + kk + 1;
+                    const double *pr = prow + kk + 2;
+                    while (i < rows) {
+                        int i2 = i + qi, j2 = j + qj;
+                        if (j2 >= wcols) { j2 -= wcols; ++i2; }
+                        double *r0 = A + prm[i] * ld + kk + 2;
+                        const double m0 = mrow[i], p0 = pr[j], a0 = r0[j];
+                        const bool two = i2 < rows;
+                        double m1 = 0.0, p1 = 0.0, a1 = 0.0;
+                        double *r1 = r0;
+                        if (two) { r1 = A + prm[i2] * ld + kk + 2; m1 = mrow[i2]; p1 = pr[j2]; a1 = r1[j2]; }
+                        r0[j] = a0 - m0 * p0;
+                        if (two) r1[j2] = a1 - m1 * p1;
+                        i = i2 + qi;
+                        j = j2 + qj;
+                        if (j >= wcols) { j -= wcols; ++i; }
+                    }
+                }
             }
-        __syncwarp();
-        // multipliers of the rows below the pivot, kept in the pivot column
-        const double inv = 1.0 / A[kk * ld + kk];
-        for (int i = kk + 1 + lane; i < S; i += 32) A[i * ld + kk] *= inv;
-        __syncwarp();
-        // A[i][j] -= m_i p_j over the (S-kk-1) x (W-kk-1) trailing block, its
-        // entries walked row by row, 32 apart per lane, two per pass
-        const int w = W - kk - 1;
-        if (w > 0) {
-            int i = kk + 1, j = kk + 1 + lane;
-            while (j >= W && i < S) { j -= w; ++i; }
-            while (i < S) {
-                int i2 = i, j2 = j + 32;
-                while (j2 >= W && i2 < S) { j2 -= w; ++i2; }
-                const double m0 = A[i * ld + kk], p0 = A[kk * ld + j], a0 = A[i * ld + j];
-                const bool two = i2 < S;
-                double m1 = 0.0, p1 = 0.0, a1 = 0.0;
-                if (two) { m1 = A[i2 * ld + kk]; p1 = A[kk * ld + j2]; a1 = A[i2 * ld + j2]; }
-                A[i * ld + j] = a0 - m0 * p0;
-                if (two) A[i2 * ld + j2] = a1 - m1 * p1;
-                i = i2;
-                j = j2 + 32;
-                while (j >= W && i < S) { j -= w; ++i; }
+            __syncthreads();
+            if (kk + 1 < S) {
+                if (s_bad[(kk + 1) & 1]) { failed = 1; break; }   // the pivot of step kk+1 (uniform)
+                cur ^= 1;
             }
         }
-        __syncwarp();
     }
-    if (singular) {
-        if (lane == 0) atomicMin(bad_node, (int)c);
+    if (failed) {
+        if (tid == 0) atomicMin(bad_node, (int)c);
         return;
     }
-    // back substitution, column-oriented: x_i = b_i / u_ii, then b_j -= u_ji x_i
+    const int *P = cur ? pm1 : pm0;   // the last step's permutation: every entry settled
     for (int i = S - 1; i >= 0; --i) {
-        if (lane < K) A[i * ld + S + lane] /= A[i * ld + i];
-        __syncwarp();
-        for (int j = lane; j < i; j += 32) {
-            double u = A[j * ld + i];
-            for (int o = 0; o < K; ++o) A[j * ld + S + o] -= u * A[i * ld + S + o];
+        if (tid < K) A[P[i] * ld + S + tid] /= diag[i];
+        __syncthreads();
+        const double *xr = A + P[i] * ld + S;
+        for (int e = tid; e < i * K; e += NT) {
+            const int j = e / K, o = e - j * K;
+            double *rj = A + P[j] * ld;
+            rj[S + o] -= rj[i] * xr[o];
         }
-        __syncwarp();
+        __syncthreads();
     }
     for (int o = 0; o < K; ++o) {
         double scale = 1.0;
         for (int t = 0; t < job.order[o]; ++t) scale *= inv_s;
-        for (int j = lane; j < n; j += 32) w[((int64_t)o * n_centers + c) * n + j] = A[j * ld + S + o] * scale;
+        for (int j = tid; j < n; j += NT) w[((int64_t)o * n_centers + c) * n + j] = A[P[j] * ld + S + o] * scale;
     }
 }
 
@@ -286,22 +336,19 @@ void build_weights(const double *x, const double *z, int64_t n_all, const int32_
     }
     if (n_centers == 0) return;
     RBF_REQUIRE(x && z && idx && w, "null pointer argument");
+    RBF_REQUIRE(n_centers <= INT_MAX, "at most %d centres per call", INT_MAX);
     job.ld = (job.S + n_ops) | 1;   // odd leading dimension: fewer bank conflicts
-    size_t per_warp = ((size_t)job.S * job.ld + 2 * n + 8) * sizeof(double);
-    // as many systems per CTA (one CTA per SM) as the 227 KB of shared memory
-    // a CTA may hold, up to 8: the SM's four sub-partitions each have their
-    // own share of the FP64 pipe, so fewer than four warps leave part of it
-    // idle (S = 77: 52 KB per system, 4 warps)
+    const size_t smem = ((size_t)job.S * job.ld + 2 * n + 4 * job.S + 8) * sizeof(double);
     int max_smem = 0, dev = 0;
     RBF_CUDA(cudaGetDevice(&dev));
     RBF_CUDA(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    int warps = (int)std::min<size_t>(8, (size_t)max_smem / per_warp);
-    RBF_REQUIRE(warps >= 1, "weight system too large for shared memory");
-    RBF_CUDA(cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(warps * per_warp)));
+    RBF_REQUIRE(smem + 1024 <= (size_t)max_smem, "weight system too large for shared memory");
+    constexpr int kThreads = 128;   // four warps per system: one look-ahead, three on the trailing block
+    RBF_CUDA(cudaFuncSetAttribute(weights_kernel<kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     DevBuf<int> bad(1);
     int init = INT_MAX;
     RBF_CUDA(cudaMemcpyAsync(bad.p, &init, sizeof(int), cudaMemcpyHostToDevice, st));
-    weights_kernel<<<div_up(n_centers, warps), warps * 32, warps * per_warp, st>>>(x, z, idx, n_centers, job, w, bad.p);
+    weights_kernel<kThreads><<<(unsigned)n_centers, kThreads, smem, st>>>(x, z, idx, n_centers, job, w, bad.p);
     RBF_CHECK_LAUNCH();
     int hb = INT_MAX;
     RBF_CUDA(cudaMemcpyAsync(&hb, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
