@@ -325,7 +325,7 @@ def headline_case(torch, args, wl, world, local, p64):
            "e2e": e2e, "gpu_launches": (1 if persistent else info["launches_per_step"]) * args.steps,
            "launch": {"run_mode": "persistent" if persistent else "graph",
                       "threads_per_node": info["threads_per_node"], "prefetch": info["prefetch"],
-                      "launches_per_step": info["launches_per_step"]},
+                      "stage_split": info["stage_split"], "launches_per_step": info["launches_per_step"]},
            "setup": {"create_s": create_s, "weight_build_ms": info["weight_build_ms"],
                      "ghost_setup_ms": info["ghost_setup_ms"]},
            "state_minmax": {"theta_max": float(mm[2, 1]), "w_min": float(mm[1, 0]), "w_max": float(mm[1, 1])}}
@@ -357,7 +357,8 @@ def bubble_fp32_case(torch, args, wl, pb64, pk, pk_kind):
                         "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg,
                         "kernel_share_of_step": float(np.sum(stage_ms) / np.sum(step_ms)),
                         "peak_source": f"{pk_kind} hbm_gbs"},
-           "threads_per_node": info["threads_per_node"], "launches_per_step": info["launches_per_step"]}
+           "threads_per_node": info["threads_per_node"], "stage_split": info["stage_split"],
+           "launches_per_step": info["launches_per_step"]}
     if not args.no_final_error:
         A32 = rbffd.state_tensor(wl.U0, 32)
         ms32 = time_run(torch, pb, A32, 0.0, wl.dt, wl.n_steps)

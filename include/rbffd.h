@@ -401,6 +401,25 @@ int rbf_run(rbf_problem *pb, double t0, double dt, int64_t n_steps, void *U);
 int rbf_set_run_mode(rbf_problem *pb, int32_t mode, int32_t lanes, int32_t ctas);
 
 /*
+ * Split stage launches of the graph mode and of rbf_rk4_step (Sec. 5.2,
+ * Eq. (bcEqn); Sec. 6.2).  The wall set is every node whose record a ghost
+ * residual reads (the wall nodes' stencils) and every node whose stencil
+ * reads a ghost.  With enable = 1 each stage runs as two launches: the other
+ * nodes on a private stream, the wall set after the stage's ghost fill.  The
+ * next stage's ghost residual and ghost solve need only the wall set, so
+ * they run while the other launch finishes.  Each node's arithmetic is
+ * unchanged, so the results are bitwise those of enable = 0.  It pays where
+ * the ghost fill is a large share of a stage (small problems) and costs a
+ * little where the stage kernel dominates, so a problem created with
+ * threads_per_node = 0 times both and keeps the faster; otherwise it is off
+ * until this call turns it on.  Stage timing (rbf_set_stage_timing) runs
+ * unsplit.
+ * Errors: RBF_E_ARG if pb is not a Navier-Stokes problem, or enable = 1 and
+ * the problem has no wall set to split (no ghosts, or every node in it).
+ */
+int rbf_set_stage_split(rbf_problem *pb, int32_t enable);
+
+/*
  * The node blocks of the persistent run mode, as a service for callers that
  * want the same decomposition: recursive coordinate bisection of the n points
  * (x, z) into `parts` blocks of equal size (+-1 node), each cut across the
@@ -498,7 +517,7 @@ typedef struct rbf_info {
     int32_t persist_chunk;      /* nodes per CTA                            */
     int32_t persist_halo_max;   /* largest per-CTA record list              */
     int32_t persist_ctas;       /* CTAs of the persistent launch            */
-    int32_t reserved2;
+    int32_t stage_split;        /* 1: split stage launches (rbf_set_stage_split) */
 } rbf_info;
 int rbf_get_info(const rbf_problem *pb, rbf_info *out);
 

@@ -33,6 +33,9 @@ int sm_count() {
 Problem::~Problem() {
     if (graph) cudaGraphExecDestroy(graph);
     for (cudaEvent_t e : rhs_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : {ev_fork, ev_w[0], ev_w[1], ev_r[0], ev_r[1]})
+        if (e) cudaEventDestroy(e);
+    if (side) cudaStreamDestroy(side);
     if (cap) cudaStreamDestroy(cap);
 }
 
@@ -134,14 +137,16 @@ void capture(Problem &pb, void *U, double dt, int steps) {
     cudaGraph_t g = nullptr;
     RBF_CUDA(cudaStreamBeginCapture(pb.cap, cudaStreamCaptureModeThreadLocal));
     try {
-        for (int s = 0; s < steps; ++s) enqueue_rk4_step(pb, 0.0, dt, U, pb.cap, pb.record_rhs_events, s);
+        for (int s = 0; s < steps; ++s)
+            enqueue_rk4_step(pb, 0.0, dt, U, pb.cap, pb.record_rhs_events, s, s == 0, s == steps - 1);
     } catch (...) {
         cudaStreamEndCapture(pb.cap, &g);
         if (g) cudaGraphDestroy(g);
         throw;
     }
     RBF_CUDA(cudaStreamEndCapture(pb.cap, &g));
-    cudaError_t e = cudaGraphInstantiate(&pb.graph, g, 0);
+    // node priorities: the split's wall-set launches go ahead of the others
+    cudaError_t e = cudaGraphInstantiateWithFlags(&pb.graph, g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     RBF_CUDA(e);
     pb.graph_U = U;
@@ -377,6 +382,7 @@ void build_ns(Problem &pb, const rbf_ns_params &prm, const double *x, const doub
     RBF_CUDA(cudaMemcpyAsync(pb.flags.p, fl.data(), n_prog, cudaMemcpyHostToDevice, pb.st));
 
     rbf::build_ghost_plan(pb, kind, ghost_owner);
+    if (with_scratch) rbf::build_wall_set(pb);
     if (with_scratch) rbf::alloc_scratch(pb);
     pb.lat.enabled = prm.storage == RBF_STORE_LATTICE;
     rbf::choose_threads(pb, prm.threads_per_node);
@@ -563,6 +569,19 @@ int rbf_set_run_mode(rbf_problem *h, int32_t mode, int32_t lanes, int32_t ctas) 
     });
 }
 
+int rbf_set_stage_split(rbf_problem *h, int32_t enable) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h, "null problem");
+        Problem &pb = h->impl;
+        RBF_REQUIRE(pb.kind == rbf::kNS, "stage splitting applies to Navier-Stokes problems");
+        RBF_REQUIRE(!enable || (pb.side && pb.wlist.p), "the problem has no wall set to split");
+        RBF_CUDA(cudaStreamSynchronize(pb.st));
+        RBF_CUDA(cudaStreamSynchronize(pb.cap));
+        rbf::invalidate_graph(pb);
+        pb.split = enable != 0;
+    });
+}
+
 int rbf_set_operator_storage(rbf_problem *h, int32_t mode, int32_t threads_per_node, int64_t *class_nodes,
                              int32_t *n_classes) {
     return rbf::guarded([&] {
@@ -614,7 +633,8 @@ int rbf_get_info(const rbf_problem *h, rbf_info *out) {
         out->threads_per_node = pb.G;
         out->slots = pb.SL * pb.G;
         const bool ghosts = pb.kind != rbf::kAdvection && pb.gh.n_ghost > 0;
-        out->launches_per_step = 4 * (ghosts ? 3 : 1) + (pb.kind == rbf::kAdvection ? 1 : 0);
+        out->launches_per_step = 4 * (ghosts ? (pb.split ? 4 : 3) : 1) + (pb.kind == rbf::kAdvection ? 1 : 0);
+        out->stage_split = pb.split ? 1 : 0;
         out->n_components = pb.gh.n_comp;
         out->n_ghost_classes = pb.gh.n_class;
         out->prefetch = pb.pf > 0 ? 1 : 0;

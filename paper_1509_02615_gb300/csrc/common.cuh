@@ -109,19 +109,37 @@ int sm_count();
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// prio != 0: the launch's scheduling priority (lower is more urgent; in a
+// captured graph it becomes the kernel node's priority, which graphs
+// instantiated with cudaGraphInstantiateFlagUseNodePriority honour).
 template <typename... KArgs, typename... Args>
-void launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, bool pdl, Args &&...args) {
+void launch_kernel_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, bool pdl, int prio,
+                        Args &&...args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = pdl ? at : nullptr;
-    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchAttribute at[2];
+    int na = 0;
+    if (pdl) {
+        at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
+    if (prio != 0) {
+        at[na].id = cudaLaunchAttributePriority;
+        at[na].val.priority = prio;
+        ++na;
+    }
+    cfg.attrs = na ? at : nullptr;
+    cfg.numAttrs = na;
     RBF_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
+
+template <typename... KArgs, typename... Args>
+void launch_kernel(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, bool pdl, Args &&...args) {
+    launch_kernel_prio(kernel, grid, block, s, pdl, 0, std::forward<Args>(args)...);
 }
 
 // ---- internal entry points shared between translation units ----------------

@@ -537,7 +537,60 @@ void build_ghost_bands(GhostPlan &gh, int precision, cudaStream_t st) {
     }
 }
 
-void enqueue_ghost_fill(Problem &pb, void *U, cudaStream_t s) {
+// The wall set: every prognostic node of a wall row's stencil (the records
+// the ghost residual reads, the wall node itself included) and every node
+// whose own stencil reads a ghost.  Only these need the stage's ghost fill
+// before, or feed the next stage's ghost fill after, their stage launch.
+void build_wall_set(Problem &pb) {
+    const int64_t np = pb.n_prog, ng = pb.gh.n_ghost;
+    const int n = pb.n;
+    if (ng == 0 || pb.kind != kNS) return;
+    std::vector<int32_t> idx((size_t)np * n), owner(ng);
+    std::vector<unsigned char> fl(np);
+    RBF_CUDA(cudaMemcpyAsync(idx.data(), pb.idx.p, idx.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, pb.st));
+    RBF_CUDA(cudaMemcpyAsync(owner.data(), pb.gh.owner.p, ng * sizeof(int32_t), cudaMemcpyDeviceToHost, pb.st));
+    RBF_CUDA(cudaMemcpyAsync(fl.data(), pb.flags.p, np, cudaMemcpyDeviceToHost, pb.st));
+    RBF_CUDA(cudaStreamSynchronize(pb.st));
+    std::vector<char> wall(np, 0);
+    for (int64_t r = 0; r < ng; ++r) {
+        const int64_t b = owner[r];
+        wall[b] = 1;
+        for (int k = 0; k < n; ++k) {
+            const int64_t j = idx[b * n + k];
+            if (j < np) wall[j] = 1;
+        }
+    }
+    for (int64_t i = 0; i < np; ++i)
+        for (int k = 0; k < n && !wall[i]; ++k)
+            if (idx[i * n + k] >= np) wall[i] = 1;
+    std::vector<int32_t> list, rest;
+    for (int64_t i = 0; i < np; ++i) {
+        if (wall[i]) {
+            list.push_back((int32_t)i);
+            fl[i] |= kWallSetFlag;
+        } else {
+            rest.push_back((int32_t)i);
+            fl[i] &= (unsigned char)~kWallSetFlag;
+        }
+    }
+    pb.n_wall = (int64_t)list.size();
+    if (pb.n_wall == 0 || pb.n_wall == np) return;   // nothing to split
+    pb.wlist.alloc(list.size());
+    pb.rlist.alloc(rest.size());
+    RBF_CUDA(cudaMemcpyAsync(pb.wlist.p, list.data(), list.size() * sizeof(int32_t), cudaMemcpyHostToDevice, pb.st));
+    RBF_CUDA(cudaMemcpyAsync(pb.rlist.p, rest.data(), rest.size() * sizeof(int32_t), cudaMemcpyHostToDevice, pb.st));
+    RBF_CUDA(cudaMemcpyAsync(pb.flags.p, fl.data(), np, cudaMemcpyHostToDevice, pb.st));
+    RBF_CUDA(cudaStreamSynchronize(pb.st));
+    if (!pb.side) RBF_CUDA(cudaStreamCreateWithFlags(&pb.side, cudaStreamNonBlocking));
+    for (cudaEvent_t *e : {&pb.ev_fork, &pb.ev_w[0], &pb.ev_w[1], &pb.ev_r[0], &pb.ev_r[1]})
+        if (!*e) RBF_CUDA(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    int least = 0, greatest = 0;
+    RBF_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    pb.prio_hi = greatest;
+    pb.split = false;   // the autotuner, or rbf_set_stage_split, turns it on
+}
+
+void enqueue_ghost_fill(Problem &pb, void *U, cudaStream_t s, int prio) {
     GhostPlan &gh = pb.gh;
     const int64_t ng = gh.n_ghost, rows = gh.rows;
     if (ng == 0 || rows == 0) return;
@@ -546,19 +599,19 @@ void enqueue_ghost_fill(Problem &pb, void *U, cudaStream_t s) {
     const int4 cf = make_int4(fields[0], fields[1], fields[2], fields[3]);
     const dim3 g1(div_up(rows * kRowLanes, 256)), g2(div_up((int64_t)gh.n_class * rows * 32, 256)), blk(256);
     if (pb.precision == 64) {
-        launch_kernel(ghost_residual<double>, g1, blk, s, pb.pdl, (const double *)U, ng, rows, gh.npad,
+        launch_kernel_prio(ghost_residual<double>, g1, blk, s, pb.pdl, prio, (const double *)U, ng, rows, gh.npad,
                       (const int32_t *)gh.gidx.p, (const double *)gh.gw.p, (const int32_t *)gh.owner.p,
                       (const unsigned char *)gh.tb.p, (const int32_t *)gh.pos.p, (double *)gh.res.p,
                       pb.cp * pb.theta_bar * pb.theta_bar, pb.theta_bar, pb.g);
-        launch_kernel(ghost_apply_band<double>, g2, blk, s, pb.pdl, (double *)U, ng, rows, gh.n_class,
+        launch_kernel_prio(ghost_apply_band<double>, g2, blk, s, pb.pdl, prio, (double *)U, ng, rows, gh.n_class,
                       (const int64_t *)gh.brow.p, (const int32_t *)gh.bcol.p, (const double *)gh.bval.p,
                       (const double *)gh.res.p, (const int64_t *)gh.grec.p, cf);
     } else {
-        launch_kernel(ghost_residual<float>, g1, blk, s, pb.pdl, (const float *)U, ng, rows, gh.npad,
+        launch_kernel_prio(ghost_residual<float>, g1, blk, s, pb.pdl, prio, (const float *)U, ng, rows, gh.npad,
                       (const int32_t *)gh.gidx.p, (const float *)gh.gw.p, (const int32_t *)gh.owner.p,
                       (const unsigned char *)gh.tb.p, (const int32_t *)gh.pos.p, (float *)gh.res.p,
                       (float)(pb.cp * pb.theta_bar * pb.theta_bar), (float)pb.theta_bar, (float)pb.g);
-        launch_kernel(ghost_apply_band<float>, g2, blk, s, pb.pdl, (float *)U, ng, rows, gh.n_class,
+        launch_kernel_prio(ghost_apply_band<float>, g2, blk, s, pb.pdl, prio, (float *)U, ng, rows, gh.n_class,
                       (const int64_t *)gh.brow.p, (const int32_t *)gh.bcol.p, (const float *)gh.bval.p,
                       (const float *)gh.res.p, (const int64_t *)gh.grec.p, cf);
     }

@@ -40,6 +40,10 @@ struct NSArgs {
     const T *wx, *wz, *wd, *wh;
     const T *pibar;
     const unsigned char *flags;
+    // split stage launches: each of the two launches takes its nodes from
+    // nlist (n_list of them; null: every node, one launch per stage)
+    const int32_t *nlist;
+    int64_t n_list;
     // lattice storage (csrc/lattice.cu): class of each node (-1: per-node
     // operators), and per class the relative index and the packed operators
     // of every slot, [4][n_cls][SLQ][G][V] (null: per-node storage only)
@@ -94,8 +98,16 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && PF == 0) ? 4 : 1) ns_s
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int g = (int)(tid % G);
     int64_t i = tid / G;
-    const bool live = i < a.n_prog;
-    if (!live) i = a.n_prog - 1;   // keep the lanes of the warp in the shuffles
+    bool live;
+    if (a.nlist) {
+        live = i < a.n_list;
+        i = __ldg(a.nlist + (live ? i : a.n_list - 1));
+    } else {
+        live = i < a.n_prog;
+        if (!live) i = a.n_prog - 1;   // keep the lanes of the warp in the shuffles
+    }
+    // lanes without a node leave unless a warp shuffle still needs them
+    if (G == 1 ? !live : !__any_sync(0xffffffffu, live)) return;
     const int64_t stride = a.n_prog * G;   // in vectors, between consecutive q
     const int64_t off0 = i * G + g;
     const I *pidx = reinterpret_cast<const I *>(a.pidx);
@@ -369,30 +381,30 @@ __global__ void minmax_kernel(const T *U, int64_t n_prog, int F, double *out, in
 }
 
 template <class T, int G, int PF>
-void launch_ns_g(const NSArgs<T> &a, cudaStream_t s, bool pdl) {
+void launch_ns_g(const NSArgs<T> &a, cudaStream_t s, bool pdl, int prio) {
     constexpr bool kDiff = sizeof(T) == 4;   // FP32: difference form; FP64: plain sums
-    const dim3 grid(div_up(a.n_prog * G, 256)), blk(256);
+    const dim3 grid(div_up((a.nlist ? a.n_list : a.n_prog) * G, 256)), blk(256);
     if (a.lcls) {
-        if (PF == 0) launch_kernel(ns_stage_kernel<T, G, kDiff, 0, true>, grid, blk, s, pdl, a);
+        if (PF == 0) launch_kernel_prio(ns_stage_kernel<T, G, kDiff, 0, true>, grid, blk, s, pdl, prio, a);
         else RBF_FAIL(RBF_E_ARG, "the lattice storage has no prefetch variant");
     } else {
-        launch_kernel(ns_stage_kernel<T, G, kDiff, PF, false>, grid, blk, s, pdl, a);
+        launch_kernel_prio(ns_stage_kernel<T, G, kDiff, PF, false>, grid, blk, s, pdl, prio, a);
     }
 }
 
 template <class T>
-void launch_ns(const NSArgs<T> &a, int G, int pf, cudaStream_t s, bool pdl) {
+void launch_ns(const NSArgs<T> &a, int G, int pf, cudaStream_t s, bool pdl, int prio = 0) {
     if (pf > 0 && a.SLQ > kPrefetchVec)
         RBF_FAIL(RBF_E_ARG, "prefetch variant needs <= %d operand vectors per lane", kPrefetchVec);
     switch (G * 2 + (pf > 0)) {
-        case 2: launch_ns_g<T, 1, 0>(a, s, pdl); break;
-        case 3: launch_ns_g<T, 1, kPrefetchVec>(a, s, pdl); break;
-        case 4: launch_ns_g<T, 2, 0>(a, s, pdl); break;
-        case 5: launch_ns_g<T, 2, kPrefetchVec>(a, s, pdl); break;
-        case 8: launch_ns_g<T, 4, 0>(a, s, pdl); break;
-        case 9: launch_ns_g<T, 4, kPrefetchVec>(a, s, pdl); break;
-        case 16: launch_ns_g<T, 8, 0>(a, s, pdl); break;
-        case 17: launch_ns_g<T, 8, kPrefetchVec>(a, s, pdl); break;
+        case 2: launch_ns_g<T, 1, 0>(a, s, pdl, prio); break;
+        case 3: launch_ns_g<T, 1, kPrefetchVec>(a, s, pdl, prio); break;
+        case 4: launch_ns_g<T, 2, 0>(a, s, pdl, prio); break;
+        case 5: launch_ns_g<T, 2, kPrefetchVec>(a, s, pdl, prio); break;
+        case 8: launch_ns_g<T, 4, 0>(a, s, pdl, prio); break;
+        case 9: launch_ns_g<T, 4, kPrefetchVec>(a, s, pdl, prio); break;
+        case 16: launch_ns_g<T, 8, 0>(a, s, pdl, prio); break;
+        case 17: launch_ns_g<T, 8, kPrefetchVec>(a, s, pdl, prio); break;
         default: RBF_FAIL(RBF_E_ARG, "threads per node %d not in {1,2,4,8}", G);
     }
 }
@@ -468,25 +480,57 @@ AdvArgs<T> adv_args(Problem &pb) {
 const double kA[4] = {0.5, 0.5, 1.0, 0.0};
 const double kB[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
 
+// One RK4 step on stream s.  With the split (pb.split, not while recording
+// stage events), each stage runs as two launches: the nodes off the wall set
+// on the side stream, the wall set (nodes whose records feed a ghost residual
+// or whose stencils read a ghost) on s after the stage's ghost fill.  The
+// ghost fill of stage st + 1 needs only the wall set of stage st, so it runs
+// while the side stream finishes stage st.  Event pairs alternate by stage
+// parity: ev_w[st & 1] marks stage st's wall set, ev_r[st & 1] the rest.
+// `first` = false continues a step sequence whose side stream is still open
+// (the previous call passed `last` = false); `last` joins the side stream
+// back into s.
 template <class T>
-void rk4_ns(Problem &pb, double dt, T *U, cudaStream_t s, bool rec, int step) {
+void rk4_ns(Problem &pb, double dt, T *U, cudaStream_t s, bool rec, int step, bool first, bool last) {
     NSArgs<T> a = ns_args<T>(pb);
     T *S0 = (T *)pb.S0.p, *S1 = (T *)pb.S1.p;
     T *in[4] = {U, S0, S1, S0};
     T *out[4] = {S0, S1, S0, U};
     a.Un = U;
     a.K = (T *)pb.K.p;
+    const bool split = pb.split && !rec;
+    if (split) {
+        RBF_CUDA(cudaEventRecord(pb.ev_fork, s));
+        RBF_CUDA(cudaStreamWaitEvent(pb.side, pb.ev_fork, 0));
+    }
     for (int st = 0; st < 4; ++st) {
-        enqueue_ghost_fill(pb, in[st], s);
         a.Uin = in[st];
         a.Uout = out[st];
         a.stage = st;
         a.a_next = (T)(kA[st] * dt);
         a.b_stage = (T)(kB[st] * dt);
+        if (split) {
+            NSArgs<T> ar = a;   // every node off the wall set
+            ar.nlist = pb.rlist.p;
+            ar.n_list = pb.n_prog - pb.n_wall;
+            if (st > 0) RBF_CUDA(cudaStreamWaitEvent(pb.side, pb.ev_w[(st - 1) & 1], 0));
+            launch_ns<T>(ar, pb.G, pb.pf, pb.side, pb.pdl);
+            RBF_CUDA(cudaEventRecord(pb.ev_r[st & 1], pb.side));
+            enqueue_ghost_fill(pb, in[st], s, pb.prio_hi);   // ahead of the other launch's blocks
+            if (st > 0 || !first) RBF_CUDA(cudaStreamWaitEvent(s, pb.ev_r[(st + 3) & 1], 0));
+            NSArgs<T> aw = a;   // the wall set, ahead of the other launch
+            aw.nlist = pb.wlist.p;
+            aw.n_list = pb.n_wall;
+            launch_ns<T>(aw, pb.G, pb.pf, s, pb.pdl, pb.prio_hi);
+            RBF_CUDA(cudaEventRecord(pb.ev_w[st & 1], s));
+            continue;
+        }
+        enqueue_ghost_fill(pb, in[st], s);
         if (rec) RBF_CUDA(cudaEventRecordWithFlags(pb.rhs_ev[(step * 4 + st) * 2], s, cudaEventRecordExternal));
         launch_ns<T>(a, pb.G, pb.pf, s, pb.pdl && !rec);
         if (rec) RBF_CUDA(cudaEventRecordWithFlags(pb.rhs_ev[(step * 4 + st) * 2 + 1], s, cudaEventRecordExternal));
     }
+    if (split && last) RBF_CUDA(cudaStreamWaitEvent(s, pb.ev_r[1], 0));
 }
 
 template <class T>
@@ -574,11 +618,12 @@ void pack_operators(Problem &pb) {
     if (pb.lat.enabled) pack_lattice(pb, comb, nops);
 }
 
-void enqueue_rk4_step(Problem &pb, double t, double dt, void *U, cudaStream_t s, bool rec, int step) {
+void enqueue_rk4_step(Problem &pb, double t, double dt, void *U, cudaStream_t s, bool rec, int step, bool first,
+                      bool last) {
     const bool tdev = (s == pb.cap);
     if (pb.kind == kNS) {
-        if (pb.precision == 64) rk4_ns<double>(pb, dt, (double *)U, s, rec, step);
-        else rk4_ns<float>(pb, dt, (float *)U, s, rec, step);
+        if (pb.precision == 64) rk4_ns<double>(pb, dt, (double *)U, s, rec, step, first, last);
+        else rk4_ns<float>(pb, dt, (float *)U, s, rec, step, first, last);
     } else {
         if (pb.precision == 64) rk4_adv<double>(pb, t, dt, (double *)U, s, tdev, rec, step);
         else rk4_adv<float>(pb, t, dt, (float *)U, s, tdev, rec, step);
@@ -623,7 +668,9 @@ void enqueue_rhs(Problem &pb, double t, void *U, void *dUdt, cudaStream_t s) {
 // Autotuner: for every (threads per node, register prefetch) choice it
 // repacks the operators and times whole RK4 steps through the real launch
 // path (ghost kernels, programmatic launches) on a zero state, then keeps the
-// fastest.  The advection problem times its right-hand side per lane count.
+// fastest; a problem with a wall set then times its steps with split stage
+// launches on and off.  The advection problem times its right-hand side per
+// lane count.
 void autotune_threads_per_node(Problem &pb) {
     const int cands[4] = {1, 2, 4, 8};
     float best = 1e30f;
@@ -658,11 +705,28 @@ void autotune_threads_per_node(Problem &pb) {
             if (ms < best) { best = ms; bestG = G; bestPf = pf; }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     pb.G = bestG;
     pb.pf = bestPf;
     pack_operators(pb);
+    if (pb.kind == kNS && pb.wlist.p) {
+        // split stage launches, on or off, timed the same way
+        float t[2] = {1e30f, 1e30f};
+        for (int on = 0; on < 2; ++on) {
+            pb.split = on != 0;
+            for (int rep = 0; rep < 3; ++rep) {
+                RBF_CUDA(cudaEventRecord(e0, pb.st));
+                for (int it = 0; it < 4; ++it) enqueue_rk4_step(pb, 0.0, 1e-3, U.p, pb.st, false, 0);
+                RBF_CUDA(cudaEventRecord(e1, pb.st));
+                RBF_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                RBF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                t[on] = std::min(t[on], ms);
+            }
+        }
+        pb.split = t[1] < t[0];
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
 }
 
 void minmax(Problem &pb, const void *U, double *out) {

@@ -57,6 +57,9 @@ struct GhostPlan {
     int64_t band_nnz = 0;
 };
 
+// flags bit of the wall set (split stage launches)
+constexpr unsigned char kWallSetFlag = 4;
+
 // Builds gh.brow / bcol / bval from the dense inverse blocks.
 void build_ghost_bands(GhostPlan &gh, int precision, cudaStream_t st);
 
@@ -133,7 +136,19 @@ struct Problem {
     DevBuf<int32_t> pidx;         // [SLQ][n_prog][G][V]
     DevBuf<unsigned char> pw;     // T [n_packed][SLQ][n_prog][G][V]
     DevBuf<unsigned char> pibar;  // T [n_prog]
-    DevBuf<unsigned char> flags;  // [n_prog]: bit0 w Dirichlet, bit1 u Dirichlet
+    DevBuf<unsigned char> flags;  // [n_prog]: bit0 w Dirichlet, bit1 u Dirichlet, bit2 wall set
+
+    // Split stage launches (graph and step modes of problems with ghosts):
+    // the wall set, the nodes whose records feed a ghost residual or whose
+    // stencils read a ghost, runs as its own launch per stage, so that the
+    // next stage's ghost fill overlaps the launch of the other nodes.
+    bool split = false;
+    DevBuf<int32_t> wlist;        // [n_wall] wall-set nodes, ascending
+    DevBuf<int32_t> rlist;        // [n_prog - n_wall] the other nodes, ascending
+    int64_t n_wall = 0;
+    int prio_hi = 0;              // scheduling priority of the wall-set launches
+    cudaStream_t side = nullptr;  // stream of the other nodes' launches
+    cudaEvent_t ev_fork = nullptr, ev_w[2] = {nullptr, nullptr}, ev_r[2] = {nullptr, nullptr};
 
     GhostPlan gh;
 
@@ -177,7 +192,11 @@ struct Problem {
 };
 
 // Launches one RK4 step (4 stages, ghost fill before each) on stream s.
-void enqueue_rk4_step(Problem &pb, double t, double dt, void *U, cudaStream_t s, bool record_events, int step_in_graph);
+// With split stage launches, a sequence of steps may leave the side stream
+// open between them: first = false continues such a sequence, last = false
+// leaves it open (the sequence's last step must pass last = true).
+void enqueue_rk4_step(Problem &pb, double t, double dt, void *U, cudaStream_t s, bool record_events, int step_in_graph,
+                      bool first = true, bool last = true);
 void enqueue_rhs(Problem &pb, double t, void *U, void *dUdt, cudaStream_t s);
 void autotune_threads_per_node(Problem &pb);
 void pack_operators(Problem &pb);
@@ -188,8 +207,15 @@ double resolve_gamma(double gamma, double gamma_c, double spacing, int hv_k);
 int32_t lattice_classes(const int32_t *idx, const double *x, const double *z, int64_t n_prog, int n,
                         double period_x, double h, int min_members, int32_t *cls);
 void build_ghost_plan(Problem &pb, const int32_t *kind_host, const int32_t *owner_host);
-void enqueue_ghost_fill(Problem &pb, void *U, cudaStream_t s);
+// Ghost residual and banded ghost solve of the state U on stream s; prio != 0
+// is the kernels' scheduling priority (see launch_kernel_prio).
+void enqueue_ghost_fill(Problem &pb, void *U, cudaStream_t s, int prio = 0);
 void minmax(Problem &pb, const void *U, double *out);
+// Split stage launches of a problem with ghosts: marks the wall set in
+// pb.flags, lists it and the other nodes in pb.wlist / pb.rlist and creates
+// the side stream and its events; the split itself stays off until the
+// autotuner or rbf_set_stage_split turns it on (csrc/ghost.cu).
+void build_wall_set(Problem &pb);
 void build_ns(Problem &pb, const rbf_ns_params &prm, const double *x, const double *z, int64_t n_prog,
               int64_t n_all, const int32_t *kind, const int32_t *ghost_owner, void *stream, bool with_scratch);
 void alloc_scratch(Problem &pb);

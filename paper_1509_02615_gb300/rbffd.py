@@ -56,7 +56,7 @@ class Info(C.Structure):
                 ("weight_build_ms", C.c_double), ("ghost_setup_ms", C.c_double),
                 ("rhs_bytes_per_node", C.c_double), ("rhs_flops_per_node", C.c_double),
                 ("persist_lanes", C.c_int32), ("persist_regs", C.c_int32), ("persist_chunk", C.c_int32),
-                ("persist_halo_max", C.c_int32), ("persist_ctas", C.c_int32), ("reserved2", C.c_int32)]
+                ("persist_halo_max", C.c_int32), ("persist_ctas", C.c_int32), ("stage_split", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -101,6 +101,7 @@ SIGNATURES = [
     ("rbf_run", C.c_int, [_P, _D, _D, _I64, _P]),
     ("rbf_run_host", C.c_int, [_P, _D, _D, _I64, _P]),
     ("rbf_set_run_mode", C.c_int, [_P, _I32, _I32, _I32]),
+    ("rbf_set_stage_split", C.c_int, [_P, _I32]),
     ("rbf_set_spin_limit", C.c_int, [_P, _I64]),
     ("rbf_set_operator_storage", C.c_int, [_P, _I32, _I32, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     ("rbf_lattice_classes", C.c_int, [_P, _P, _P, _I64, _I64, _I32, _D, _D, _I32, _P, C.POINTER(C.c_int32)]),
@@ -239,6 +240,11 @@ class Problem:
     def set_run_mode(self, mode, lanes=0, ctas=0):
         """'graph', 'persistent' or 'auto' (see rbf_set_run_mode)."""
         _check(lib().rbf_set_run_mode(self._h, self.RUN_MODES[mode], int(lanes), int(ctas)))
+
+    def set_stage_split(self, enable):
+        """Split each stage into a wall-set launch and the rest, so that the
+        next stage's ghost fill overlaps the rest (see rbf_set_stage_split)."""
+        _check(lib().rbf_set_stage_split(self._h, int(bool(enable))))
 
     def set_operator_storage(self, mode, threads_per_node=0):
         """'per-node' (Sec. 3's rows) or 'lattice' (one row per class of
