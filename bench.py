@@ -302,7 +302,8 @@ def headline_case(torch, args, wl, world, local, p64):
     ach = flops / (avg_ms / 1e3) / 1e12
     key = f"ns_stage_fp64_bubble{int(nodes.h)}"
     roof = {"bound": "alu", "achieved": ach, "peak": p64, "unit": "TFLOP/s", "frac": ach / p64,
-            "traffic": None if persistent else profiled_traffic(key, threads_per_node=info["threads_per_node"]),
+            "traffic": None if persistent else profiled_traffic(key, threads_per_node=info["threads_per_node"],
+                                                                stage_split=info["stage_split"]),
             "kernel": kernel, "algorithmic_flops_per_launch": flops,
             "algorithmic_bytes_per_launch": info["rhs_bytes_per_node"] * nodes.n_prog * (4 if persistent else 1),
             "avg_launch_ms": avg_ms, "kernel_share_of_step": share,
@@ -353,7 +354,7 @@ def bubble_fp32_case(torch, args, wl, pb64, pk, pk_kind):
            "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                         "frac": ach / pk["hbm_gbs"], "kernel": "ns_stage_kernel<float>",
                         "traffic": profiled_traffic(f"ns_stage_fp32_bubble{int(nodes.h)}",
-                                                    threads_per_node=info["threads_per_node"]),
+                                                    threads_per_node=info["threads_per_node"], stage_split=info["stage_split"]),
                         "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg,
                         "kernel_share_of_step": float(np.sum(stage_ms) / np.sum(step_ms)),
                         "peak_source": f"{pk_kind} hbm_gbs"},
@@ -594,12 +595,12 @@ def large_case(torch, args, flush):
     several times larger than L2: the stage kernel's HBM roofline."""
     from paper_1509_02615_gb300 import rbffd
     pk, pk_kind = peaks()
-    nodes, pb, U0 = make_dc_problem(args.large_h, 32)
+    nodes, pb, U0 = make_dc_problem(args.large_h, 32, tpn=args.threads_per_node)
     info = pb.info()
     U = rbffd.state_tensor(U0, 32)
     dt = args.large_h / 400.0
     steps = 10
-    step_ms, _ = time_steps(torch, pb, U, dt, steps, 3, flush, False)
+    step_ms, _ = time_steps(torch, pb, U, dt, steps, 3, flush, False, nvtx="large_timed")
     _, stage_ms = time_steps(torch, pb, U, dt, steps, 1, flush, True)
     avg = float(np.mean(stage_ms)) / 4.0
     bpl = info["rhs_bytes_per_node"] * nodes.n_prog
@@ -609,7 +610,7 @@ def large_case(torch, args, flush):
            "ms_per_step": float(sum(step_ms)) / steps,
            "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                         "frac": ach / pk["hbm_gbs"], "traffic": profiled_traffic(f"ns_stage_fp32_hex{int(args.large_h)}",
-                                                                   threads_per_node=info["threads_per_node"]),
+                                                                   threads_per_node=info["threads_per_node"], stage_split=info["stage_split"]),
                         "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg,
                         "peak_source": f"{pk_kind} hbm_gbs"},
            "threads_per_node": info["threads_per_node"], "prefetch": info["prefetch"],
@@ -618,11 +619,11 @@ def large_case(torch, args, flush):
     # class of translated stencils); its bytes per node-RHS follow the storage
     Ur = U.clone()
     t0 = time.perf_counter()
-    cn, nc = pb.set_operator_storage("lattice")
+    cn, nc = pb.set_operator_storage("lattice", args.threads_per_node)
     lat_setup_s = time.perf_counter() - t0
     li = pb.info()
     Ul = rbffd.state_tensor(U0, 32)
-    lstep, _ = time_steps(torch, pb, Ul, dt, steps, 3, flush, False)
+    lstep, _ = time_steps(torch, pb, Ul, dt, steps, 3, flush, False, nvtx="large_lattice_timed")
     _, lstage = time_steps(torch, pb, Ul, dt, steps, 1, flush, True)
     lavg = float(np.mean(lstage)) / 4.0
     lbpl = li["rhs_bytes_per_node"] * nodes.n_prog
@@ -637,7 +638,7 @@ def large_case(torch, args, flush):
         "rhs_bytes_per_node": li["rhs_bytes_per_node"], "threads_per_node": li["threads_per_node"],
         "roofline": {"bound": "hbm", "achieved": lach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": lach / pk["hbm_gbs"], "traffic": profiled_traffic(f"ns_stage_lattice_fp32_hex{int(args.large_h)}",
-                                                                threads_per_node=li["threads_per_node"]),
+                                                                threads_per_node=li["threads_per_node"], stage_split=li["stage_split"]),
                      "algorithmic_bytes_per_launch": lbpl, "avg_launch_ms": lavg,
                      "peak_source": f"{pk_kind} hbm_gbs",
                      "note": "algorithmic bytes of the lattice storage: class id + records, no per-node operators"},
