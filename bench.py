@@ -302,8 +302,7 @@ def headline_case(torch, args, wl, world, local, p64):
     ach = flops / (avg_ms / 1e3) / 1e12
     key = f"ns_stage_fp64_bubble{int(nodes.h)}"
     roof = {"bound": "alu", "achieved": ach, "peak": p64, "unit": "TFLOP/s", "frac": ach / p64,
-            "traffic": None if persistent else profiled_traffic(key, threads_per_node=info["threads_per_node"],
-                                                                stage_split=info["stage_split"]),
+            "traffic": None if persistent else profiled_traffic(key, threads_per_node=info["threads_per_node"]),
             "kernel": kernel, "algorithmic_flops_per_launch": flops,
             "algorithmic_bytes_per_launch": info["rhs_bytes_per_node"] * nodes.n_prog * (4 if persistent else 1),
             "avg_launch_ms": avg_ms, "kernel_share_of_step": share,
@@ -354,7 +353,7 @@ def bubble_fp32_case(torch, args, wl, pb64, pk, pk_kind):
            "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                         "frac": ach / pk["hbm_gbs"], "kernel": "ns_stage_kernel<float>",
                         "traffic": profiled_traffic(f"ns_stage_fp32_bubble{int(nodes.h)}",
-                                                    threads_per_node=info["threads_per_node"], stage_split=info["stage_split"]),
+                                                    threads_per_node=info["threads_per_node"]),
                         "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg,
                         "kernel_share_of_step": float(np.sum(stage_ms) / np.sum(step_ms)),
                         "peak_source": f"{pk_kind} hbm_gbs"},
@@ -610,10 +609,11 @@ def large_case(torch, args, flush):
            "ms_per_step": float(sum(step_ms)) / steps,
            "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                         "frac": ach / pk["hbm_gbs"], "traffic": profiled_traffic(f"ns_stage_fp32_hex{int(args.large_h)}",
-                                                                   threads_per_node=info["threads_per_node"], stage_split=info["stage_split"]),
+                                                                   threads_per_node=info["threads_per_node"]),
                         "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg,
                         "peak_source": f"{pk_kind} hbm_gbs"},
            "threads_per_node": info["threads_per_node"], "prefetch": info["prefetch"],
+           "stage_split": info["stage_split"],
            "setup": {"weight_build_ms": info["weight_build_ms"], "ghost_setup_ms": info["ghost_setup_ms"]}}
     # f4: the same steps with lattice operator storage (one operator row per
     # class of translated stencils); its bytes per node-RHS follow the storage
@@ -638,7 +638,7 @@ def large_case(torch, args, flush):
         "rhs_bytes_per_node": li["rhs_bytes_per_node"], "threads_per_node": li["threads_per_node"],
         "roofline": {"bound": "hbm", "achieved": lach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": lach / pk["hbm_gbs"], "traffic": profiled_traffic(f"ns_stage_lattice_fp32_hex{int(args.large_h)}",
-                                                                threads_per_node=li["threads_per_node"], stage_split=li["stage_split"]),
+                                                                threads_per_node=li["threads_per_node"]),
                      "algorithmic_bytes_per_launch": lbpl, "avg_launch_ms": lavg,
                      "peak_source": f"{pk_kind} hbm_gbs",
                      "note": "algorithmic bytes of the lattice storage: class id + records, no per-node operators"},
