@@ -62,3 +62,23 @@ def test_split_needs_a_wall_set():
     pb = rbffd.advection_problem(wl.nodes, precision=64, **wl.params)
     with pytest.raises(rbffd.RBFError):
         pb.set_stage_split(True)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_split_with_lattice_storage(precision):
+    """The split's two node lists with lattice operator storage (class nodes
+    read the class table, the others their own rows): bitwise the unsplit
+    lattice run, on the hexagonal density current."""
+    wl = configs.density_current(400.0)
+    pb = rbffd.ns_problem(wl.nodes, precision=precision, threads_per_node=1, storage="lattice", **wl.params)
+    pb.set_run_mode("graph")
+    out = {}
+    for split in (True, False):
+        pb.set_stage_split(split)
+        A = rbffd.state_tensor(wl.U0, precision)
+        pb.run(0.0, wl.dt, 21, A)
+        pb.sync()
+        assert torch.all(torch.isfinite(A))
+        out[split] = A
+    assert pb.info()["stage_split"] == 0
+    assert torch.equal(out[True], out[False])
