@@ -328,6 +328,16 @@ int rbf_mlp_forward(rbf_mlp *m, const void *U, void *delta);
  */
 int rbf_learned_run(rbf_mlp *m, double t0, double dt, int64_t n_steps, const double *alpha, void *U,
                     int64_t *n_fallback);
+/*
+ * Chooses the coarse problem's persistent plan (lanes per node, CTAs) for
+ * corrected runs: times short corrected runs of the fused persistent kernel
+ * on a zero state for lanes 1, 2, 4 and one CTA per SM, per 2, 4 or 8 SMs,
+ * and keeps the fastest.  The problem's run mode becomes persistent with that
+ * plan (rbf_run uses it too; rbf_get_info reports it).  Synchronous.
+ * Errors: RBF_E_ARG if no persistent kernel holding the network fits the
+ * problem (FP64 problems, or too many nodes for one co-resident grid).
+ */
+int rbf_mlp_tune_run(rbf_mlp *m);
 int rbf_mlp_destroy(rbf_mlp *m);
 /*
  * Restriction by injection (device): for e < n_map, record

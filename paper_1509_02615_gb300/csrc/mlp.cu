@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <vector>
 #include <cstring>
 
 #include "problem.cuh"
@@ -28,6 +29,7 @@ namespace rbf {
 
 constexpr int kWidth = 64;
 constexpr int kTrainBlock = 128;
+constexpr int kScaleWarps = 2048;   // warps of the scale-sum launch (256 blocks of 256 threads)
 constexpr float kClip = 4.f;   // |y| <= 4 (in output-scale units) when the correction is applied
 
 struct Mlp {
@@ -36,6 +38,7 @@ struct Mlp {
     int64_t oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;
     cudaStream_t st = nullptr;
     DevBuf<float> P, Gr, M, V, scales, loss;
+    DevBuf<float> Gp, Lp;     // per-block gradient and loss partials of a training launch
     DevBuf<__nv_bfloat16> Pb;
     DevBuf<double> acc;       // scale sums
     DevBuf<unsigned long long> bad;
@@ -221,14 +224,18 @@ struct TrainArgs {
     const __nv_bfloat16 *Pb;
     const float *P;
     const float *scales;
-    float *G;
-    float *loss;          // loss accumulator of this iteration
+    float *Gp;            // [blocks][n_params]: this block's weight gradients
+    int64_t n_params;
+    float *Lp;            // [blocks]: this block's loss
 };
 
 // Fused gather + forward + backward for one block of 128 samples; the block's
-// weight gradients (X^T dH1, H1^T dH2, H2^T dY and bias sums) are added to G.
+// weight gradients (X^T dH1, H1^T dH2, H2^T dY and bias sums) and loss go to
+// its own partials, which mlp_reduce_kernel sums over the blocks in block
+// order (so training is deterministic).
 __global__ void __launch_bounds__(kTrainBlock) mlp_train_kernel(TrainArgs a, Offs m_off) {
     extern __shared__ unsigned char sm[];
+    float *const gp = a.Gp + blockIdx.x * a.n_params;
     const int n_in = 4 * (a.n - 1) + 4;
     const int xs = n_in + 1;                 // padded row strides (bank spread)
     const int hs = kWidth + 1;
@@ -324,7 +331,7 @@ __global__ void __launch_bounds__(kTrainBlock) mlp_train_kernel(TrainArgs a, Off
         if (t < w) red[t] += red[t + w];
         __syncthreads();
     }
-    if (t == 0) atomicAdd(a.loss, red[0]);
+    if (t == 0) a.Lp[blockIdx.x] = red[0];
     // the f(0) branch enters y with the opposite sign: its output gradient is
     // dz = -sum dY over the block, propagated back through z2 and z1
     if (t < 4) {
@@ -351,11 +358,11 @@ __global__ void __launch_bounds__(kTrainBlock) mlp_train_kernel(TrainArgs a, Off
         if (o < kWidth * 4) {
             const int m = o >> 2, c = o & 3;
             for (int q = 0; q < kTrainBlock; ++q) acc += H2[q * hs + m] * DY[q * 4 + c];
-            atomicAdd(a.G + m_off.oW3 + o, acc + z2[m] * dz[c]);
+            gp[m_off.oW3 + o] = acc + z2[m] * dz[c];
         } else {
             const int c = o - kWidth * 4;
             for (int q = 0; q < kTrainBlock; ++q) acc += DY[q * 4 + c];
-            atomicAdd(a.G + m_off.ob3 + c, acc + dz[c]);
+            gp[m_off.ob3 + c] = acc + dz[c];
         }
     }
     __syncthreads();
@@ -374,11 +381,11 @@ __global__ void __launch_bounds__(kTrainBlock) mlp_train_kernel(TrainArgs a, Off
         if (o < kWidth * kWidth) {
             const int m = o / kWidth, j = o % kWidth;
             for (int q = 0; q < kTrainBlock; ++q) acc += H1[q * hs + m] * H2[q * hs + j];
-            atomicAdd(a.G + m_off.oW2 + o, acc + z1[m] * dz2[j]);
+            gp[m_off.oW2 + o] = acc + z1[m] * dz2[j];
         } else {
             const int j = o - kWidth * kWidth;
             for (int q = 0; q < kTrainBlock; ++q) acc += H2[q * hs + j];
-            atomicAdd(a.G + m_off.ob2 + j, acc + dz2[j]);
+            gp[m_off.ob2 + j] = acc + dz2[j];
         }
     }
     __syncthreads();
@@ -406,12 +413,29 @@ __global__ void __launch_bounds__(kTrainBlock) mlp_train_kernel(TrainArgs a, Off
         if (o < n_in * kWidth) {
             const int r = o / kWidth, j = o % kWidth;
             for (int q = 0; q < kTrainBlock; ++q) acc += X[q * xs + r] * H1[q * hs + j];
-            atomicAdd(a.G + m_off.oW1 + o, acc);
+            gp[m_off.oW1 + o] = acc;
         } else {
             const int j = o - n_in * kWidth;
             for (int q = 0; q < kTrainBlock; ++q) acc += H1[q * hs + j];
-            atomicAdd(a.G + m_off.ob1 + j, acc + dz1[j]);
+            gp[m_off.ob1 + j] = acc + dz1[j];
         }
+    }
+}
+
+// G = sum over the blocks of their gradient partials, and the iteration's
+// loss = sum of the blocks' losses, both in block order.
+__global__ void mlp_reduce_kernel(const float *Gp, const float *Lp, int nb, int64_t n_params, float *G,
+                                  float *loss) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p < n_params) {
+        float g = 0.f;
+        for (int b = 0; b < nb; ++b) g += Gp[b * n_params + p];
+        G[p] = g;
+    }
+    if (p == 0) {
+        float l = 0.f;
+        for (int b = 0; b < nb; ++b) l += Lp[b];
+        *loss = l;
     }
 }
 
@@ -435,8 +459,9 @@ __global__ void to_bf16(const float *P, __nv_bfloat16 *Pb, int64_t n) {
     if (p < n) Pb[p] = __float2bfloat16_rn(P[p]);
 }
 
-// sums for the scales: acc[f] += squared stencil differences of field f,
-// acc[4+f] += squared targets of field f, acc[8+f] += squared own values
+// sums for the scales, one row of 12 per warp (the host adds the rows in warp
+// order, so the scales do not depend on the warps' timing): [f] squared
+// stencil differences of field f, [4+f] squared targets, [8+f] squared own values
 __global__ void mlp_scale_sums(const float *S, const float *Tg, int64_t n_states, int64_t n_snap, int64_t n_all,
                                int64_t n_prog, const int32_t *idx, int n, double *acc) {
     double a[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
@@ -458,7 +483,7 @@ __global__ void mlp_scale_sums(const float *S, const float *Tg, int64_t n_states
     for (int c = 0; c < 12; ++c) {
         double v = a[c];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) atomicAdd(acc + c, v);
+        if ((threadIdx.x & 31) == 0) acc[((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 12 + c] = v;
     }
 }
 
@@ -532,9 +557,15 @@ void mlp_launch_train(Mlp &m, Problem &pb, const float *S, const float *Tg, int6
     a.Pb = m.Pb.p;
     a.P = m.P.p;
     a.scales = m.scales.p;
-    a.G = m.Gr.p;
-    a.loss = loss;
-    mlp_train_kernel<<<div_up(B, kTrainBlock), kTrainBlock, train_smem(m.n_in), m.st>>>(a, offs_of(m));
+    const int nb = div_up(B, kTrainBlock);
+    if (m.Gp.n < (size_t)nb * m.n_params) m.Gp.alloc((size_t)nb * m.n_params);
+    if (m.Lp.n < (size_t)nb) m.Lp.alloc(nb);
+    a.Gp = m.Gp.p;
+    a.n_params = m.n_params;
+    a.Lp = m.Lp.p;
+    mlp_train_kernel<<<nb, kTrainBlock, train_smem(m.n_in), m.st>>>(a, offs_of(m));
+    RBF_CHECK_LAUNCH();
+    mlp_reduce_kernel<<<div_up(m.n_params, 256), 256, 0, m.st>>>(m.Gp.p, m.Lp.p, nb, m.n_params, m.Gr.p, loss);
     RBF_CHECK_LAUNCH();
 }
 
@@ -561,7 +592,7 @@ void mlp_init(Mlp &m, Problem &pb, void *stream) {
     m.V.alloc(m.n_params);
     m.Pb.alloc(m.n_params);
     m.scales.alloc(12);
-    m.acc.alloc(12);
+    m.acc.alloc(12 * kScaleWarps);
     m.bad.alloc(1);
     RBF_CUDA(cudaMemsetAsync(m.P.p, 0, m.P.bytes(), m.st));
     RBF_CUDA(cudaMemsetAsync(m.Gr.p, 0, m.Gr.bytes(), m.st));
@@ -655,13 +686,15 @@ int rbf_mlp_fit_scales(rbf_mlp *h, const float *states, const float *targets, in
         const int64_t n_states = n_runs * (n_snap - 1);
         Mlp &m = h->impl;
         rbf::Problem &pb = h->coarse->impl;
-        RBF_CUDA(cudaMemsetAsync(m.acc.p, 0, 12 * sizeof(double), m.st));
-        rbf::mlp_scale_sums<<<256, 256, 0, m.st>>>(states, targets, n_states, n_snap, pb.n_all, pb.n_prog, pb.idx.p,
-                                                 m.n, m.acc.p);
+        rbf::mlp_scale_sums<<<rbf::kScaleWarps / 8, 256, 0, m.st>>>(states, targets, n_states, n_snap, pb.n_all,
+                                                                   pb.n_prog, pb.idx.p, m.n, m.acc.p);
         RBF_CHECK_LAUNCH();
-        double s[12];
-        RBF_CUDA(cudaMemcpyAsync(s, m.acc.p, sizeof(s), cudaMemcpyDeviceToHost, m.st));
+        std::vector<double> rows(12 * rbf::kScaleWarps);
+        RBF_CUDA(cudaMemcpyAsync(rows.data(), m.acc.p, rows.size() * sizeof(double), cudaMemcpyDeviceToHost, m.st));
         RBF_CUDA(cudaStreamSynchronize(m.st));
+        double s[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int w = 0; w < rbf::kScaleWarps; ++w)
+            for (int c = 0; c < 12; ++c) s[c] += rows[(size_t)w * 12 + c];
         float sc[12];
         const double cnt_in = (double)n_states * pb.n_prog * (m.n - 1), cnt_out = (double)n_states * pb.n_prog;
         for (int c = 0; c < 4; ++c) {
@@ -721,6 +754,32 @@ int rbf_mlp_forward(rbf_mlp *h, const void *U, void *delta) {
     });
 }
 
+// The network as the persistent kernel reads it, with strengths alpha.
+static rbf::MlpView mlp_view(Mlp &m, const double *alpha) {
+    rbf::MlpView mv{};
+    mv.Pb = m.Pb.p;
+    mv.P = m.P.p;
+    mv.oW1 = m.oW1; mv.ob1 = m.ob1; mv.oW2 = m.oW2; mv.ob2 = m.ob2; mv.oW3 = m.oW3; mv.ob3 = m.ob3;
+    mv.scales = m.scales.p;
+    for (int f = 0; f < 4; ++f) mv.alpha[f] = (float)alpha[f];
+    mv.n_in = m.n_in;
+    mv.bad = m.bad.p;
+    return mv;
+}
+
+int rbf_mlp_tune_run(rbf_mlp *h) {
+    return rbf::guarded([&] {
+        RBF_REQUIRE(h, "null argument");
+        Mlp &m = h->impl;
+        rbf::Problem &pb = h->coarse->impl;
+        RBF_CUDA(cudaStreamSynchronize(pb.st));
+        RBF_CUDA(cudaStreamSynchronize(pb.cap));
+        const double ones[4] = {1.0, 1.0, 1.0, 1.0};
+        RBF_REQUIRE(rbf::persistent_tune_mlp(pb, mlp_view(m, ones)),
+                    "no persistent kernel with the network fits this problem");
+    });
+}
+
 int rbf_learned_run(rbf_mlp *h, double t0, double dt, int64_t n_steps, const double *alpha, void *U,
                     int64_t *n_fallback) {
     return rbf::guarded([&] {
@@ -734,14 +793,7 @@ int rbf_learned_run(rbf_mlp *h, double t0, double dt, int64_t n_steps, const dou
         if (pb.run_mode == RBF_RUN_PERSISTENT && rbf::persistent_mlp_ready(pb)) {
             // the whole corrected run in one persistent launch (network evaluated
             // at stage 0 of every step from the records in shared memory)
-            rbf::MlpView mv{};
-            mv.Pb = m.Pb.p;
-            mv.P = m.P.p;
-            mv.oW1 = m.oW1; mv.ob1 = m.ob1; mv.oW2 = m.oW2; mv.ob2 = m.ob2; mv.oW3 = m.oW3; mv.ob3 = m.ob3;
-            mv.scales = m.scales.p;
-            for (int f = 0; f < 4; ++f) mv.alpha[f] = (float)alpha[f];
-            mv.n_in = m.n_in;
-            mv.bad = m.bad.p;
+            const rbf::MlpView mv = mlp_view(m, alpha);
             rbf::persistent_run_mlp(pb, dt, n_steps, U, pb.st, mv);
             unsigned long long bad = 0;
             RBF_CUDA(cudaMemcpyAsync(&bad, m.bad.p, sizeof(bad), cudaMemcpyDeviceToHost, pb.st));

@@ -1401,6 +1401,73 @@ extern "C" int rbf_partition_blocks(const double *x, const double *z, int64_t n,
 
 namespace rbf {
 
+// Persistent plan for corrected runs.  The network's phase changes which plan
+// is fastest (4 lanes per node and a CTA per 4 SMs for the 400 m coarse
+// density current, where the plain run prefers 2 lanes), so corrected runs
+// are timed directly: 8 steps on a zero state (the network is evaluated in
+// full; its correction f(x) - f(0) is zero there), best of three, for lanes
+// 1, 2, 4 and one CTA per SM, per 2, 4 or 8 SMs.
+bool persistent_tune_mlp(Problem &pb, const MlpView &mv) {
+    if (pb.kind != kNS || pb.precision != 32 || !pb.S0.p) return false;
+    const int nsm = sm_count();
+    int dev = 0, optin = 0;
+    RBF_CUDA(cudaGetDevice(&dev));
+    RBF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const size_t bytes = (size_t)pb.F * pb.n_all * sizeof(float);
+    DevBuf<unsigned char> U(bytes);
+    RBF_CUDA(cudaMemsetAsync(U.p, 0, bytes, pb.st));
+    cudaEvent_t e0, e1;
+    RBF_CUDA(cudaEventCreate(&e0));
+    RBF_CUDA(cudaEventCreate(&e1));
+    const int steps = 8;
+    float best = 1e30f;
+    int bG = 0, bC = 0;
+    try {
+        for (int G : {1, 2, 4}) {
+            for (int div : {1, 2, 4, 8}) {
+                const int c = nsm / div;
+                if (c < 1 || (div > 1 && (int64_t)c * 8 > pb.n_prog)) continue;
+                if (!persistent_plan(pb, G, c) || !persistent_mlp_ready(pb)) continue;
+                if (pb.ps.smem + mlp_layout(mv.n_in, pb.ps.chunk, pb.n_slots).end > (size_t)optin) continue;
+                persistent_run_mlp(pb, 1e-3, steps, U.p, pb.st, mv);   // warm-up
+                float t = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    RBF_CUDA(cudaEventRecord(e0, pb.st));
+                    persistent_run_mlp(pb, 1e-3, steps, U.p, pb.st, mv);
+                    RBF_CUDA(cudaEventRecord(e1, pb.st));
+                    RBF_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    RBF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    t = std::min(t, ms);
+                }
+                persistent_check(pb);
+                if (t < best) {
+                    best = t;
+                    bG = G;
+                    bC = c;
+                }
+            }
+        }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (bG == 0 || !persistent_plan(pb, bG, bC)) {
+        pb.ps.ready = false;
+        pb.run_mode = RBF_RUN_GRAPH;
+        return false;
+    }
+    pb.run_mode = RBF_RUN_PERSISTENT;
+    // zero the stage buffers the timing runs wrote (ghost records included)
+    RBF_CUDA(cudaMemsetAsync(pb.S0.p, 0, pb.S0.bytes(), pb.st));
+    RBF_CUDA(cudaMemsetAsync(pb.S1.p, 0, pb.S1.bytes(), pb.st));
+    RBF_CUDA(cudaStreamSynchronize(pb.st));
+    return true;
+}
+
 void persistent_check(Problem &pb) {
     if (pb.ps.abort.n == 0) return;
     int v = 0;

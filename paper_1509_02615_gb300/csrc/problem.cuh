@@ -245,6 +245,10 @@ struct MlpView {
 // persistent mode with a variant that holds the network).
 bool persistent_mlp_ready(const Problem &pb);
 void persistent_run_mlp(Problem &pb, double dt, int64_t n_steps, void *U, cudaStream_t s, const MlpView &mv);
+// Persistent plan for corrected runs: times short corrected runs on a zero
+// state for each lane count and CTA count, keeps the fastest plan that holds
+// the network and puts the problem in persistent mode; false if none fits.
+bool persistent_tune_mlp(Problem &pb, const MlpView &mv);
 // RBF_E_TIMEOUT (and clears the flag) if a persistent launch gave up a wait.
 void persistent_check(Problem &pb);
 

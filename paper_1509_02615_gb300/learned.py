@@ -95,13 +95,15 @@ def init_params(n_in: int, width: int = 64, seed: int = 0) -> np.ndarray:
 
 
 def train(ds: Dataset, n_train: int, iters: int = 2000, batch: int = 4096, lr: float = 2e-3, seed: int = 0):
-    """Fits feature scales on the training runs and trains the MLP."""
+    """Fits feature scales on the training runs, trains the MLP and chooses
+    the coarse problem's persistent plan for corrected runs."""
     mlp = rbffd.Mlp(ds.coarse)
     n_in = 4 * (ds.coarse.info()["n_sten"] - 1) + 4   # differences, then own values
     mlp.set_params(init_params(n_in, seed=seed))
     S, T = ds.states[:n_train], ds.targets[:n_train]
     mlp.fit_scales(S, T, n_train, ds.n_snap)
     loss = mlp.train(S, T, n_train, ds.n_snap, iters, batch=batch, lr=lr, seed=seed)
+    mlp.tune_run()   # the coarse problem's persistent plan, timed for corrected runs
     return mlp, loss
 
 

@@ -91,6 +91,7 @@ SIGNATURES = [
     ("rbf_mlp_train", C.c_int, [_P, _P, _P, _I64, _I64, _I64, _I32, C.c_float, C.c_uint64, _P]),
     ("rbf_mlp_forward", C.c_int, [_P, _P, _P]),
     ("rbf_learned_run", C.c_int, [_P, _D, _D, _I64, _P, _P, C.POINTER(C.c_int64)]),
+    ("rbf_mlp_tune_run", C.c_int, [_P]),
     ("rbf_mlp_destroy", C.c_int, [_P]),
     ("rbf_restrict", C.c_int, [_P, _I32, _P, _I64, _P, _I32, _I64, _I64, _P]),
     ("rbf_restrict_weighted", C.c_int, [_P, _I32, _P, _P, _I32, _I64, _P, _I64, _I64, _P]),
@@ -510,6 +511,13 @@ class Mlp:
             delta = _torch().empty((self.coarse.n_prog, 4), dtype=U.dtype, device="cuda")
         _check(lib().rbf_mlp_forward(self._h, _ptr(U), _ptr(delta)))
         return delta
+
+    def tune_run(self):
+        """Persistent plan of the coarse problem chosen for corrected runs
+        (rbf_mlp_tune_run); returns (lanes per node, CTAs)."""
+        _check(lib().rbf_mlp_tune_run(self._h))
+        i = self.coarse.info()
+        return i["persist_lanes"], i["persist_ctas"]
 
     def run(self, t0, dt, n_steps, U, alpha=(1.0, 1.0, 1.0, 1.0)):
         """Corrected coarse run (U_f += alpha_f dt delta_f after each step);

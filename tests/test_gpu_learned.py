@@ -140,3 +140,25 @@ def test_correction_on_held_out_seeds():
     assert np.all(np.isfinite(el))
     assert any(a > 0.0 for a in alpha), alpha
     assert np.mean(el) < 0.85 * np.mean(ep), (np.mean(el), np.mean(ep))
+
+
+def test_training_is_deterministic(small_data):
+    """Per-block gradient partials summed in block order, and the scale sums
+    added per warp in warp order: two trainings from the same data and seed
+    give the same scales, losses and parameters, bit for bit."""
+    nodes, S, T, idx, R, n_snap = small_data
+    pb = rbffd.ns_problem(nodes, precision=32, threads_per_node=1)
+    St = torch.as_tensor(S, device="cuda")
+    Tt = torch.as_tensor(T, device="cuda")
+    out = []
+    for _ in range(2):
+        mlp = rbffd.Mlp(pb)
+        mlp.set_params(learned.init_params(4 * 36 + 4, seed=3))
+        mlp.fit_scales(St, Tt, R, n_snap)
+        loss = mlp.train(St, Tt, R, n_snap, 300, batch=512, lr=2e-3, seed=5)
+        out.append((mlp.scales(), loss, mlp.params()))
+        mlp.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
+    assert np.all(np.isfinite(out[0][1])) and out[0][1][-1] < out[0][1][0]

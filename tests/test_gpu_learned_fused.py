@@ -46,9 +46,9 @@ def _setup(h, lanes, ctas):
     return nodes, pb, mlp, U0
 
 
-@pytest.mark.parametrize("h,lanes,ctas", [(800.0, 1, 0), (400.0, 4, 38), (400.0, 2, 76)])
-def test_fused_learned_run_matches_standalone(h, lanes, ctas):
-    nodes, pb, mlp, U0 = _setup(h, lanes, ctas)
+def _fused_against_standalone(h, nodes, pb, mlp, U0, label):
+    """40 corrected steps fused (the problem's persistent plan) and through the
+    stand-alone kernels (graph mode), and the plain run beside them."""
     dt, steps, alpha = h / 400.0, 40, (0.5, 0.5, 1.0, 0.25)
     A = rbffd.state_tensor(U0, 32)
     nf = mlp.run(0.0, dt, steps, A, alpha=alpha)            # persistent mode: fused
@@ -64,11 +64,30 @@ def test_fused_learned_run_matches_standalone(h, lanes, ctas):
     pb.sync()
     c = rbffd.fields(C)[:, :P]
     effect = [rel(b[f], c[f]) for f in range(4)]
-    print(f"h={h} lanes={lanes}: fused vs stand-alone {['%.1e' % e for e in errs]}; "
+    print(f"{label}: fused vs stand-alone {['%.1e' % e for e in errs]}; "
           f"correction effect {['%.1e' % e for e in effect]}")
     assert nf == 0 and nb == 0
     assert max(errs) < 1e-5, errs
     assert min(effect) > 100 * max(errs)
+
+
+@pytest.mark.parametrize("h,lanes,ctas", [(800.0, 1, 0), (400.0, 4, 38), (400.0, 2, 76)])
+def test_fused_learned_run_matches_standalone(h, lanes, ctas):
+    nodes, pb, mlp, U0 = _setup(h, lanes, ctas)
+    _fused_against_standalone(h, nodes, pb, mlp, U0, f"h={h} lanes={lanes}")
+
+
+def test_tuned_plan_matches_standalone():
+    """rbf_mlp_tune_run chooses the persistent plan of corrected runs by timing
+    them; on the chosen plan the fused run still agrees with the stand-alone
+    path."""
+    nodes, pb, mlp, U0 = _setup(400.0, 2, 38)
+    lanes, ctas = mlp.tune_run()
+    info = pb.info()
+    print(f"tuned plan: {lanes} lanes per node, {ctas} CTAs of {info['persist_chunk']} nodes")
+    assert lanes in (1, 2, 4) and 1 <= ctas <= torch.cuda.get_device_properties(0).multi_processor_count
+    assert info["run_mode"] == 2
+    _fused_against_standalone(400.0, nodes, pb, mlp, U0, f"tuned {lanes} lanes, {ctas} CTAs")
 
 
 def test_fused_zero_strength_is_the_plain_run():
