@@ -883,6 +883,14 @@ def learned_case(torch, args):
                     for c in curve if c["precision"] == 64)
     t64 = cost_at(64, e_l)
     t32 = cost_at(32, e_l)
+
+    def speedup_floor(prec):
+        """Learned error below every plain run of a precision: the most
+        accurate plain run's time over the learned time, a lower bound on the
+        speedup at equal error (a plain run as accurate would be finer still)."""
+        pts = [c for c in curve if c["precision"] == prec]
+        best = min(pts, key=lambda c: c["rel_l2_mean"])
+        return best["ms_to_900s"] / ms_learned if e_l <= best["rel_l2_mean"] else None
     mid = [c for c in curve if c["precision"] == 64 and abs(c["h_m"] - hc / 2.0) < 1e-6][0]
     out = {"workload": f"density current, hexagonal {hc:g} m coarse ({nc} nodes), MLP trained on {hc / ratio:g} m FP64 "
                        f"runs restricted to the coarse nodes ({n_train} train / {n_val} validation / {len(test)} test "
@@ -914,7 +922,10 @@ def learned_case(torch, args):
                             "fp64_ms_at_learned_error": t64,
                             "speedup_vs_fp64_at_learned_error": None if t64 is None else t64 / ms_learned,
                             "fp32_ms_at_learned_error": t32,
-                            "speedup_vs_fp32_at_learned_error": None if t32 is None else t32 / ms_learned},
+                            "speedup_vs_fp32_at_learned_error": None if t32 is None else t32 / ms_learned,
+                            "learned_error_below_every_plain_run": speedup_floor(64) is not None,
+                            "speedup_vs_fp64_at_least": speedup_floor(64),
+                            "speedup_vs_fp32_at_least": speedup_floor(32)},
            "final_training_loss": float(np.mean(loss[-50:])),
            "seconds": {"data": t_data, "train": t_train}}
     mlp.close()
