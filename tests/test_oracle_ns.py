@@ -19,7 +19,8 @@
   derivatives at O(h^l)).
 * Linear stability about rest at the coarsest resolution of the Sec. 6.3 time
   step table (800 m, dt = 2 s): every eigenvalue of dt * Jacobian lies in
-  RK4's stability region up to a small growth factor.
+  RK4's stability region up to a small growth factor; 21-node stencils
+  (degree 3) have a mode far outside it, 25-node ones do not.
 * Table straka (slow): loose agreement with the printed extrema and front
   location at 800 m and 400 m.
 """
@@ -110,10 +111,10 @@ def test_rk4_amplification_polynomial():
         assert abs(out[0, 0] - R.real) < 1e-14 and abs(out[1, 0] - np.imag(R)) < 1e-14
 
 
-def test_linear_stability_at_800m(dc800):
-    nodes, o = dc800
+def _worst_rk4_amplification(nodes, o, dt):
+    """Largest |R(dt lambda)| over the eigenvalues lambda of the right-hand
+    side linearised about rest (R the RK4 amplification polynomial)."""
     n = nodes.n_prog
-    dt = 2.0
     eps = 1e-7
     J = np.zeros((4 * n, 4 * n))
     for c in range(4 * n):
@@ -121,9 +122,31 @@ def test_linear_stability_at_800m(dc800):
         U[c // n, c % n] = eps
         J[:, c] = o.rhs(0.0, U).ravel() / eps
     z = np.linalg.eigvals(J * dt)
-    R = np.abs(1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24)
+    return np.abs(1 + z + z ** 2 / 2 + z ** 3 / 6 + z ** 4 / 24).max()
+
+
+def test_linear_stability_at_800m(dc800):
+    nodes, o = dc800
+    R = _worst_rk4_amplification(nodes, o, 2.0)
     # 450 steps to 900 s: the worst mode may grow by at most 10% over the run
-    assert R.max() ** 450 < 1.1, R.max()
+    assert R ** 450 < 1.1, R
+
+
+@pytest.mark.parametrize("layout", ["hex", "cart"])
+def test_21_node_stencils_are_linearly_unstable(layout):
+    """Why the ensemble draw has no 21-node stencils: with r^7 and degree 3
+    (n close to twice the 10 monomials, the pairing the paper's summary
+    recommends) the operator linearised about rest has a mode outside RK4's
+    region at dt = h/400 for either hyperviscosity order and a four times
+    larger constant, while 25 nodes with the same degree are stable."""
+    from paper_1509_02615_gb300 import inputs as ens
+    assert min(n for n, _ in ens.ENSEMBLE_STENCILS) > 21
+    nodes = inp.density_current_nodes(800.0, layout=layout)
+    for k, c in ((3, 2.0 ** -6), (3, 2.0 ** -4), (2, 2.0 ** -6)):
+        R = _worst_rk4_amplification(nodes, NSOracle(nodes, n=21, l=3, hv_k=k, gamma_c=c), 2.0)
+        assert R > 1.05, (k, c, R)   # grows by more than e^21 over 450 steps
+    R = _worst_rk4_amplification(nodes, NSOracle(nodes, n=25, l=3), 2.0)
+    assert R ** 450 < 1.1, R
 
 
 @pytest.mark.slow
