@@ -478,8 +478,15 @@ def advection_case(torch):
         P = rbffd.state_tensor(wl.U0, prec)
         ms = time_run(torch, pb, P, 0.0, wl.dt, wl.n_steps)
         psi = rbffd.fields(P)[0]
+        info = pb.info()
+        persistent = info["run_mode"] == 2
         out[f"fp{prec}"] = {"value": 4.0 * n * wl.n_steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / wl.n_steps,
-                            "return_error_rel_l2": float(np.linalg.norm(psi - wl.U0) / np.linalg.norm(wl.U0))}
+                            "return_error_rel_l2": float(np.linalg.norm(psi - wl.U0) / np.linalg.norm(wl.U0)),
+                            "run_mode": "persistent" if persistent else "graph",
+                            "threads_per_node": info["threads_per_node"],
+                            "launches_per_run": 1 if persistent else info["launches_per_step"] * wl.n_steps}
+        if persistent:
+            out[f"fp{prec}"]["persistent_ctas"] = info["persist_ctas"]
         pb.close()
     return out
 

@@ -386,9 +386,10 @@ int rbf_rk4_step(rbf_problem *pb, double t, double dt, void *U);
 int rbf_run(rbf_problem *pb, double t0, double dt, int64_t n_steps, void *U);
 
 /*
- * Run modes of rbf_run for Navier-Stokes problems.
+ * Run modes of rbf_run for Navier-Stokes and scalar advection problems.
  *   RBF_RUN_GRAPH       ghost residual, ghost solve and fused stage kernels
- *                       per stage, captured once and replayed as a graph.
+ *                       per stage (advection: the stage kernel alone),
+ *                       captured once and replayed as a graph.
  *   RBF_RUN_PERSISTENT  one cooperative launch runs every step: one CTA per
  *                       SM owns a contiguous slice of nodes, copies the
  *                       records its stencils read into shared memory each
@@ -397,13 +398,23 @@ int rbf_run(rbf_problem *pb, double t0, double dt, int64_t n_steps, void *U);
  *                       Eqs. (uEq)-(piEq), RK4).  Results equal the graph
  *                       mode's with the same lanes per node.  Available when
  *                       every node fits one co-resident grid.
+ *                       Advection problems (Sec. 6.1, RK4): every lane
+ *                       keeps its packed slots in registers, each stage
+ *                       gathers the stage input through L2 and the CTAs
+ *                       meet at a grid barrier; results equal the graph
+ *                       mode's bit for bit with the same lanes per node.
  *   RBF_RUN_AUTO        time both on a zero state and keep the faster
- *                       (done at creation when threads_per_node is 0).
- * lanes: lanes per node of the persistent kernel (1, 2 or 4; 0 = fastest).
+ *                       (done at creation when threads_per_node is 0, and
+ *                       always for advection problems).
+ * lanes: lanes per node of the persistent kernel (Navier-Stokes 1, 2 or 4;
+ *        advection 2, 4 or 8, which also become the lanes of the graph
+ *        mode; 0 = fastest).
  * ctas:  CTAs of the persistent kernel (0: fastest of 1, 1/2, 1/4, 1/8 per
  *        SM; with lanes > 0 and RBF_RUN_PERSISTENT, one per SM untimed).
- * Errors: RBF_E_ARG if the mode is unknown, the problem is not a
- * Navier-Stokes problem, or RBF_RUN_PERSISTENT does not fit.
+ *        Advection problems take 0: their CTA count follows from the lanes
+ *        and the fastest CTA size (64, 128 or 256 threads).
+ * Errors: RBF_E_ARG if the mode or an argument is out of range, the problem
+ * is an ensemble, or RBF_RUN_PERSISTENT does not fit.
  */
 #define RBF_RUN_AUTO 0
 #define RBF_RUN_GRAPH 1

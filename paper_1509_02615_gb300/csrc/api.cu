@@ -160,7 +160,11 @@ void run(Problem &pb, double t0, double dt, int64_t n_steps, void *U) {
     RBF_REQUIRE(n_steps >= 0, "n_steps < 0");
     RBF_REQUIRE(std::isfinite(dt) && std::isfinite(t0), "non-finite time or step");
     if (n_steps == 0) return;
-    if (pb.run_mode == RBF_RUN_PERSISTENT && pb.ps.ready && !pb.record_rhs_events) {
+    if (pb.kind == kAdvection && pb.run_mode == RBF_RUN_PERSISTENT && pb.ps.ready && !pb.record_rhs_events) {
+        adv_persistent_run(pb, t0, dt, n_steps, U, pb.st);
+        return;
+    }
+    if (pb.kind == kNS && pb.run_mode == RBF_RUN_PERSISTENT && pb.ps.ready && !pb.record_rhs_events) {
         // the equations are autonomous: t0 does not enter the launch
         persistent_run(pb, dt, n_steps, U, pb.st);
         return;
@@ -214,12 +218,76 @@ float time_run(Problem &pb, void *U, int steps) {
     return best;
 }
 
+// Run-mode autotuner of an advection problem: graph replay (with the lanes
+// per node it was packed for) against the persistent kernel for 2, 4 and 8
+// lanes per node (operators repacked for each) and CTAs of 64, 128 and 256
+// threads, on a zero state; keeps the fastest.  lanes > 0 restricts the
+// persistent candidates to that lane count.
+void choose_run_mode_adv(Problem &pb, int mode, int lanes, int ctas) {
+    RBF_REQUIRE(mode == RBF_RUN_AUTO || mode == RBF_RUN_GRAPH || mode == RBF_RUN_PERSISTENT,
+                "unknown run mode %d", mode);
+    RBF_REQUIRE(lanes == 0 || lanes == 2 || lanes == 4 || lanes == 8,
+                "lanes must be 0, 2, 4 or 8 for an advection problem");
+    RBF_REQUIRE(ctas == 0, "the CTA count of an advection problem follows from its lanes and CTA size (ctas = 0)");
+    invalidate_graph(pb);
+    if (mode == RBF_RUN_GRAPH) {
+        pb.run_mode = RBF_RUN_GRAPH;
+        pb.ps.ready = false;
+        return;
+    }
+    const int G0 = pb.G;
+    const size_t bytes = (size_t)pb.n_prog * pb.tsize();
+    DevBuf<unsigned char> U(bytes);
+    RBF_CUDA(cudaMemsetAsync(U.p, 0, bytes, pb.st));
+    const int steps = 8;
+    float best = 1e30f;
+    int bG = 0, bT = 0;
+    if (mode == RBF_RUN_AUTO) {
+        pb.run_mode = RBF_RUN_GRAPH;
+        pb.ps.ready = false;
+        best = time_run(pb, U.p, steps);
+        invalidate_graph(pb);
+    }
+    for (int G : {2, 4, 8}) {
+        if (lanes && G != lanes) continue;
+        pb.G = G;
+        pack_operators(pb);
+        for (int threads : {64, 128, 256}) {
+            if (!adv_persistent_plan(pb, threads)) continue;
+            pb.run_mode = RBF_RUN_PERSISTENT;
+            const float t = time_run(pb, U.p, steps);
+            if (t < best) {
+                best = t;
+                bG = G;
+                bT = threads;
+            }
+        }
+    }
+    pb.ps.ready = false;
+    pb.run_mode = RBF_RUN_GRAPH;
+    if (bG == 0) {
+        pb.G = G0;
+        pack_operators(pb);
+        RBF_REQUIRE(mode == RBF_RUN_AUTO, "the persistent kernel does not fit this problem");
+        return;
+    }
+    pb.G = bG;
+    pack_operators(pb);
+    RBF_REQUIRE(adv_persistent_plan(pb, bT), "persistent plan failed");
+    pb.run_mode = RBF_RUN_PERSISTENT;
+    RBF_CUDA(cudaStreamSynchronize(pb.st));
+}
+
 // Run-mode autotuner: graph replay against the persistent kernel for each
 // (lanes per node, CTA count) that fits, on a zero state; keeps the fastest.
 // lanes > 0 restricts the persistent candidates to that lane count, ctas > 0
 // to that CTA count; with both given (RBF_RUN_PERSISTENT) nothing is timed.
 void choose_run_mode(Problem &pb, int mode, int lanes, int ctas) {
-    RBF_REQUIRE(pb.kind == kNS, "run modes apply to Navier-Stokes problems");
+    if (pb.kind == kAdvection) {
+        choose_run_mode_adv(pb, mode, lanes, ctas);
+        return;
+    }
+    RBF_REQUIRE(pb.kind == kNS, "run modes apply to Navier-Stokes and advection problems");
     RBF_REQUIRE(mode == RBF_RUN_AUTO || mode == RBF_RUN_GRAPH || mode == RBF_RUN_PERSISTENT,
                 "unknown run mode %d", mode);
     RBF_REQUIRE(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4, "lanes must be 0, 1, 2 or 4");
@@ -497,6 +565,7 @@ int rbf_adv_create_flow(rbf_problem **out, const rbf_adv_params *prm, const doub
             cudaEventDestroy(e1);
             rbf::alloc_scratch(pb);
             rbf::choose_threads(pb, 0);
+            rbf::choose_run_mode(pb, RBF_RUN_AUTO, 0, 0);
             RBF_CUDA(cudaStreamSynchronize(pb.st));
             *out = h;
         } catch (...) {
@@ -638,7 +707,7 @@ int rbf_get_info(const rbf_problem *h, rbf_info *out) {
         out->n_components = pb.gh.n_comp;
         out->n_ghost_classes = pb.gh.n_class;
         out->prefetch = pb.pf > 0 ? 1 : 0;
-        out->run_mode = pb.kind == rbf::kNS ? pb.run_mode : RBF_RUN_GRAPH;
+        out->run_mode = pb.kind == rbf::kEnsemble ? RBF_RUN_GRAPH : pb.run_mode;
         if (pb.ps.ready) {
             out->persist_lanes = pb.ps.G;
             out->persist_regs = pb.ps.R > 0 ? 1 : 0;

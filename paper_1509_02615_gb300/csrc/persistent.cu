@@ -805,6 +805,105 @@ __global__ void __launch_bounds__(MAXT, 1) rk4_persistent(const __grid_constant_
     }
 }
 
+// a6 + a7 in one launch: a whole rbf_run of a scalar advection problem
+// (Sec. 6.1, flux form with the reflections folded into the stencil
+// indices).  Its problems are small (4,096 nodes for the deformational flow
+// on 64 x 64), so the launch-per-stage form is bound by launch latency.
+// Here each lane keeps its R packed slots (stencil index, flux weights of
+// each velocity part, hyperviscosity weight) in registers for the whole run,
+// U_n and the RK4 accumulator of its node too; a stage gathers the stage
+// input through L2, forms the tendency and the RK4 update exactly as the
+// stage kernel does (same slots per lane, summation order, lane reduction,
+// time factors and update), and the CTAs meet at a grid barrier.  Results
+// equal the launch-per-stage form's bit for bit with the same lanes per node.
+template <class T>
+struct AdvPArgs {
+    T *U, *S0, *S1;                // [n_prog] scalar state and stage buffers
+    const int32_t *pidx;           // packed as for the stage kernel: [SL][n_prog][G]
+    const T *wa, *wa2, *wh;
+    int64_t n_prog;
+    int SL;
+    T an[3], bs[4];                // RK4: stage s writes U_n + an[s] k_s, accumulates bs[s] k_s
+    double t0, dt, frac[4], period_T;
+    double fa[2], fb[2], fm[2];
+    int64_t n_steps;
+    unsigned *arrive;
+    unsigned base;
+    int *abort;
+    long long spin_limit;
+};
+
+template <class T, int G, int R, int NP>
+__global__ void __launch_bounds__(256, 1) adv_persistent(const __grid_constant__ AdvPArgs<T> a) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int g = (int)(tid % G);
+    int64_t i = tid / G;
+    const bool live = i < a.n_prog;
+    if (!live) i = a.n_prog - 1;   // idle lanes mirror the last node and write nothing
+    const int64_t stride = a.n_prog * G;
+    int jr[R];
+    T ra[R], rb[R], rh[R];
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+        const int64_t off = i * G + g + s * stride;
+        const bool in = s < a.SL;
+        jr[s] = in ? __ldg(a.pidx + off) : 0;
+        ra[s] = in ? __ldg(a.wa + off) : T(0);
+        rb[s] = (in && NP == 2) ? __ldg(a.wa2 + off) : T(0);
+        rh[s] = in ? __ldg(a.wh + off) : T(0);
+    }
+    T un = __ldcg(a.U + i), K = 0, o = 0;
+    double tcur = a.t0;
+    unsigned target = a.base;
+    // velocity time factors of the step's four stage times, formed once per
+    // CTA (FP64 cos is costly on this part's FP64 pipe) while the other warps
+    // gather stage 0's inputs
+    __shared__ double s_ff[4][2];
+    for (int64_t step = 0; step < a.n_steps; ++step) {
+        if (threadIdx.x < 4 * NP) {
+            const int st = threadIdx.x / NP, k = threadIdx.x % NP;
+            s_ff[st][k] = flow_factor(a.fa[k], a.fb[k], a.fm[k], tcur + a.frac[st], a.period_T);
+        }
+        for (int st = 0; st < 4; ++st) {
+            const T *Uin = st == 0 ? a.U : st == 2 ? a.S1 : a.S0;
+            T *Uout = st == 0 ? a.S0 : st == 1 ? a.S1 : st == 2 ? a.S0 : a.U;
+            T sa = 0, sb = 0, sh = 0;
+#pragma unroll
+            for (int s = 0; s < R; ++s) {
+                if (s < a.SL) {
+                    const T v = __ldcg(Uin + jr[s]);   // written by other CTAs in this launch: through L2
+                    sa += ra[s] * v;
+                    if (NP == 2) sb += rb[s] * v;
+                    sh += rh[s] * v;
+                }
+            }
+#pragma unroll
+            for (int q = G / 2; q > 0; q >>= 1) {
+                sa += __shfl_xor_sync(0xffffffffu, sa, q, G);
+                if (NP == 2) sb += __shfl_xor_sync(0xffffffffu, sb, q, G);
+                sh += __shfl_xor_sync(0xffffffffu, sh, q, G);
+            }
+            if (st == 0) __syncthreads();   // s_ff of this step (later stages: after the grid barrier)
+            T kf = (T)s_ff[st][0] * sa + sh;
+            if (NP == 2) kf += (T)s_ff[st][1] * sb;
+            if (st == 0) {
+                K = a.bs[0] * kf;
+                o = un + a.an[0] * kf;
+            } else if (st < 3) {
+                K += a.bs[st] * kf;
+                o = un + a.an[st] * kf;
+            } else {
+                o = un + (K + a.bs[3] * kf);
+                un = o;
+            }
+            if (live && g == 0) Uout[i] = o;
+            const bool last = step + 1 == a.n_steps && st == 3;
+            if (!last && !grid_barrier(a.arrive, a.abort, target, a.spin_limit)) return;
+        }
+        tcur += a.dt;
+    }
+}
+
 // Kernel variants: (lanes per node, operand vectors held in registers,
 // thread limit).  The register variant covers FP32 stencils of up to 36
 // packed slots with one lane per node; the others read their operands each
@@ -1347,6 +1446,118 @@ void persistent_run(Problem &pb, double dt, int64_t n_steps, void *U, cudaStream
     // barrier of the ghost-solving CTAs in every stage
     ps.base += (unsigned)((uint64_t)ps.grid * (uint64_t)(4 * n_steps - 1));
     if (ps.own_rows) ps.base2 += (unsigned)((uint64_t)ps.wall_ctas * (uint64_t)(4 * n_steps));
+}
+
+// ---- advection (a6 + a7): plan, launch and choice of lanes and CTA size -------
+
+// Register-resident slots per lane of each lane count: a 37-node stencil
+// needs 19 (2 lanes), 10 (4 lanes) or 5 (8 lanes).
+constexpr int kAdvR2 = 19, kAdvR4 = 10, kAdvR8 = 5;
+
+template <class T, int NP>
+void *adv_fn(int G) {
+    switch (G) {
+        case 2: return (void *)adv_persistent<T, 2, kAdvR2, NP>;
+        case 4: return (void *)adv_persistent<T, 4, kAdvR4, NP>;
+        case 8: return (void *)adv_persistent<T, 8, kAdvR8, NP>;
+    }
+    return nullptr;
+}
+
+void *adv_variant(const Problem &pb, int G) {
+    if (pb.precision == 64) return pb.n_vparts == 2 ? adv_fn<double, 2>(G) : adv_fn<double, 1>(G);
+    return pb.n_vparts == 2 ? adv_fn<float, 2>(G) : adv_fn<float, 1>(G);
+}
+
+int adv_regs(int G) { return G == 2 ? kAdvR2 : G == 4 ? kAdvR4 : G == 8 ? kAdvR8 : 0; }
+
+// Plan for the problem's current packing (pb.G lanes per node) with CTAs of
+// `threads` threads; false if the slots of a lane exceed the variant's
+// registers or the grid does not fit one co-resident launch.
+bool adv_persistent_plan(Problem &pb, int threads) {
+    PersistPlan &ps = pb.ps;
+    ps.ready = false;
+    if (pb.kind != kAdvection || !pb.S0.p) return false;
+    if (threads != 64 && threads != 128 && threads != 256) return false;
+    const int G = pb.G;
+    if (adv_regs(G) == 0 || pb.SL > adv_regs(G)) return false;
+    int dev = 0, coop = 0;
+    RBF_CUDA(cudaGetDevice(&dev));
+    RBF_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return false;
+    void *fn = adv_variant(pb, G);
+    const int64_t grid = div_up(pb.n_prog * G, threads);
+    int per_sm = 0;
+    RBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0));
+    if (grid > (int64_t)per_sm * sm_count()) return false;
+    ps.G = G;
+    ps.R = pb.SL;
+    ps.maxt = 256;
+    ps.chunk = threads / G;
+    ps.threads = threads;
+    ps.grid = (int)grid;
+    ps.halo_max = 0;
+    ps.rows_max = 0;
+    ps.smem = 0;
+    ps.own_rows = false;
+    if (ps.arrive.n == 0) ps.arrive.alloc(1);
+    RBF_CUDA(cudaMemset(ps.arrive.p, 0, sizeof(unsigned)));
+    ps.base = 0;
+    if (ps.abort.n == 0) {
+        ps.abort.alloc(1);
+        RBF_CUDA(cudaMemset(ps.abort.p, 0, sizeof(int)));
+    }
+    ps.ready = true;
+    return true;
+}
+
+template <class T>
+void adv_launch(Problem &pb, double t0, double dt, int64_t n_steps, T *U, cudaStream_t s) {
+    PersistPlan &ps = pb.ps;
+    AdvPArgs<T> a{};
+    const int64_t total = (int64_t)pb.SL * pb.G * pb.n_prog;
+    const T *pw = (const T *)pb.pw.p;
+    a.U = U;
+    a.S0 = (T *)pb.S0.p;
+    a.S1 = (T *)pb.S1.p;
+    a.pidx = pb.pidx.p;
+    a.wa = pw;
+    a.wa2 = pb.n_vparts == 2 ? pw + total : pw;
+    a.wh = pw + pb.n_vparts * total;
+    a.n_prog = pb.n_prog;
+    a.SL = pb.SL;
+    // the stage kernels' RK4 coefficients and stage times, formed the same way
+    const double cA[3] = {0.5, 0.5, 1.0}, cB[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+    const double fr[4] = {0.0, 0.5, 0.5, 1.0};
+    for (int k = 0; k < 3; ++k) a.an[k] = (T)(cA[k] * dt);
+    for (int k = 0; k < 4; ++k) a.bs[k] = (T)(cB[k] * dt);
+    for (int k = 0; k < 4; ++k) a.frac[k] = fr[k] * dt;
+    a.t0 = t0;
+    a.dt = dt;
+    a.period_T = pb.period_T;
+    for (int k = 0; k < 2; ++k) {
+        a.fa[k] = pb.vpart[k][0];
+        a.fb[k] = pb.vpart[k][1];
+        a.fm[k] = pb.vpart[k][2];
+    }
+    a.n_steps = n_steps;
+    a.arrive = ps.arrive.p;
+    a.base = ps.base;
+    a.abort = ps.abort.p;
+    a.spin_limit = ps.spin_limit;
+    void *fn = adv_variant(pb, ps.G);
+    RBF_REQUIRE(fn != nullptr, "persistent advection variant missing");
+    void *args[] = {&a};
+    RBF_CUDA(cudaLaunchCooperativeKernel(fn, dim3(ps.grid), dim3(ps.threads), args, 0, s));
+    // one barrier after every stage but the last
+    ps.base += (unsigned)((uint64_t)ps.grid * (uint64_t)(4 * n_steps - 1));
+}
+
+void adv_persistent_run(Problem &pb, double t0, double dt, int64_t n_steps, void *U, cudaStream_t s) {
+    RBF_REQUIRE(pb.ps.ready && pb.ps.G == pb.G && pb.ps.R == pb.SL, "no persistent plan for this packing");
+    if (n_steps <= 0) return;
+    if (pb.precision == 64) adv_launch<double>(pb, t0, dt, n_steps, (double *)U, s);
+    else adv_launch<float>(pb, t0, dt, n_steps, (float *)U, s);
 }
 
 bool persistent_mlp_ready(const Problem &pb) {

@@ -57,6 +57,12 @@ struct GhostPlan {
     int64_t band_nnz = 0;
 };
 
+// Time factor c_k(t) = a + b cos(m pi t / T) of a separable velocity part
+// (advection, Sec. 6.1); both advection run modes evaluate it this way.
+__device__ __forceinline__ double flow_factor(double a, double b, double m, double t, double T) {
+    return b == 0.0 ? a : a + b * cos(m * 3.141592653589793 * t / T);
+}
+
 // flags bit of the wall set (split stage launches)
 constexpr unsigned char kWallSetFlag = 4;
 
@@ -229,6 +235,11 @@ double ensemble_node_updates(const Problem &pb, int64_t max_steps);
 // tells the same).
 bool persistent_plan(Problem &pb, int G, int ctas);
 void persistent_run(Problem &pb, double dt, int64_t n_steps, void *U, cudaStream_t s);
+// Advection (a6 + a7) in one cooperative launch: the plan for the problem's
+// current packing (pb.G lanes per node, operators in registers) with CTAs of
+// `threads` threads (64, 128 or 256); false if it does not fit.
+bool adv_persistent_plan(Problem &pb, int threads);
+void adv_persistent_run(Problem &pb, double t0, double dt, int64_t n_steps, void *U, cudaStream_t s);
 
 // a9 fused into the persistent run: the learned correction's network (BF16
 // weights, FP32 biases and scales) and its per-field strengths.
