@@ -156,9 +156,10 @@ def test_run_mode_arguments():
     assert e.value.code == rbffd.RBF_E_ARG
     with pytest.raises(rbffd.RBFError):
         pb.set_spin_limit(-1)
+    # advection problems have a persistent form of their own, with 2, 4 or 8 lanes
     adv = rbffd.advection_problem(inp.unit_square_mirrored(16), precision=64)
     with pytest.raises(rbffd.RBFError) as e:
-        adv.set_run_mode("persistent")
+        adv.set_run_mode("persistent", lanes=1)
     assert e.value.code == rbffd.RBF_E_ARG
 
 
