@@ -233,6 +233,10 @@ struct AdvArgs {
     double fa[2], fb[2], fm[2];
 };
 
+__device__ __forceinline__ double flow_factor(double a, double b, double m, double t, double T) {
+    return b == 0.0 ? a : a + b * cos(m * 3.141592653589793 * t / T);
+}
+
 template <class T, int G, int NP>
 __global__ void __launch_bounds__(256) adv_stage_kernel(AdvArgs<T> a) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

@@ -151,12 +151,17 @@ __device__ __forceinline__ void st_relaxed(int *p, int v) {
 // comparison tolerates wrap-around, so the counter is never reset between
 // launches).  Returns false if this or another CTA gave up; the caller then
 // returns.
+//
+// Ordering: the CTA barrier orders every thread's stage outputs before
+// thread 0's arrival, a release add at gpu scope; the poll that sees the last
+// arrival is an acquire at gpu scope, and the closing CTA barrier orders it
+// before every thread's next reads.  Release and acquire are cumulative
+// through the CTA barriers, so no separate fences are needed.
 __device__ bool grid_barrier(unsigned *arrive, int *abort, unsigned &target, long long limit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         target += gridDim.x;
-        __threadfence();
         red_release_add(arrive, 1u);
         int ok = 1;
         long long polls = 0;
@@ -170,7 +175,6 @@ __device__ bool grid_barrier(unsigned *arrive, int *abort, unsigned &target, lon
             __nanosleep(32);
         }
         if (ok && ld_relaxed(abort)) ok = 0;
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -184,7 +188,6 @@ __device__ bool group_barrier(unsigned *arrive, int *abort, unsigned &target, un
     __syncthreads();
     if (threadIdx.x == 0) {
         target += members;
-        __threadfence();
         red_release_add(arrive, 1u);
         int ok = 1;
         long long polls = 0;
@@ -198,7 +201,6 @@ __device__ bool group_barrier(unsigned *arrive, int *abort, unsigned &target, un
             __nanosleep(32);
         }
         if (ok && ld_relaxed(abort)) ok = 0;
-        __threadfence();
         s_ok2 = ok;
     }
     __syncthreads();
@@ -862,7 +864,7 @@ __global__ void __launch_bounds__(256, 1) adv_persistent(const __grid_constant__
     for (int64_t step = 0; step < a.n_steps; ++step) {
         if (threadIdx.x < 4 * NP) {
             const int st = threadIdx.x / NP, k = threadIdx.x % NP;
-            s_ff[st][k] = flow_factor(a.fa[k], a.fb[k], a.fm[k], tcur + a.frac[st], a.period_T);
+            s_ff[st][k] = velocity_time_factor(a.fa[k], a.fb[k], a.fm[k], tcur + a.frac[st], a.period_T);
         }
         for (int st = 0; st < 4; ++st) {
             const T *Uin = st == 0 ? a.U : st == 2 ? a.S1 : a.S0;

@@ -58,8 +58,10 @@ struct GhostPlan {
 };
 
 // Time factor c_k(t) = a + b cos(m pi t / T) of a separable velocity part
-// (advection, Sec. 6.1); both advection run modes evaluate it this way.
-__device__ __forceinline__ double flow_factor(double a, double b, double m, double t, double T) {
+// (advection, Sec. 6.1), as the persistent advection kernel evaluates it.  It
+// is the same expression as the stage kernel's flow_factor (csrc/ns.cu), so
+// the two run modes agree bit for bit (tests/test_gpu_adv_persistent.py).
+__device__ __forceinline__ double velocity_time_factor(double a, double b, double m, double t, double T) {
     return b == 0.0 ? a : a + b * cos(m * 3.141592653589793 * t / T);
 }
 
