@@ -26,3 +26,18 @@ def test_profiled_traffic_matches_source_and_launch_shape(tmp_path, monkeypatch)
     assert bench.profiled_traffic("persistent_fp32_hex100", persistent_lanes=1, persistent_ctas=152) == 7
     assert bench.profiled_traffic("persistent_fp32_hex100", persistent_lanes=2, persistent_ctas=152) is None
     assert bench.profiled_traffic("missing_key") is None
+
+
+def test_committed_traffic_entries_name_their_captures():
+    """Every committed traffic figure points at an ncu summary under
+    profiles/ and records the launch shape it was taken with."""
+    import os
+    with open(bench.TRAFFIC_JSON) as f:
+        d = json.load(f)
+    assert d
+    for key, e in d.items():
+        assert len(e["source_hash"]) == 16, key
+        assert ("dram_bytes_per_launch" in e) != ("dram_per_algorithmic_byte" in e), key
+        capture = e["capture"].split()[0]
+        assert capture.startswith("profiles/") and os.path.exists(os.path.join(bench.ROOT, capture)), key
+        assert "threads_per_node" in e or "persistent_lanes" in e, key
