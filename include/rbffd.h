@@ -524,7 +524,8 @@ typedef struct rbf_info {
     int64_t n_prog, n_all, n_ghost;
     int32_t n_fields, precision, n_sten, threads_per_node;
     int32_t slots;              /* packed neighbour slots per node          */
-    int32_t launches_per_step;  /* kernel launches in one RK4 step          */
+    int32_t launches_per_step;  /* kernel launches in one RK4 step of the
+                                   graph mode (a persistent run is one launch) */
     int32_t n_components;       /* independent ghost systems                */
     int32_t n_ghost_classes;    /* distinct ghost matrices per component    */
     int32_t prefetch;           /* 1: stage kernel holds operands in registers */
@@ -536,7 +537,8 @@ typedef struct rbf_info {
     int32_t persist_lanes;      /* persistent kernel: lanes per node (0: none) */
     int32_t persist_regs;       /* 1: it keeps its operands in registers    */
     int32_t persist_chunk;      /* nodes per CTA                            */
-    int32_t persist_halo_max;   /* largest per-CTA record list              */
+    int32_t persist_halo_max;   /* largest per-CTA record list (0 for
+                                   advection, which gathers through L2)      */
     int32_t persist_ctas;       /* CTAs of the persistent launch            */
     int32_t stage_split;        /* 1: split stage launches (rbf_set_stage_split) */
 } rbf_info;
